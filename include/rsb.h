@@ -1,0 +1,184 @@
+/*
+ * rsb.h — C ABI of librsb: Recursive Spectral Bisection of element dual graphs
+ * on one GPU (sm_103a).
+ *
+ * Method (Ratnayaka & Fischer, "parRSB: Exascale Spectral Element Mesh
+ * Partitioning"):
+ *   - the problem statement (§2): a graph G(V, E) with positive edge weights
+ *     and a part count P; find disjoint V_1..V_P covering V whose sizes differ
+ *     by at most one (the printed "= 1" is read as "<= 1");
+ *   - the weighted Laplacian L = D - A (§4) and its action (§5, assembled form);
+ *   - the Fiedler vector (§4, Eqs. eigen0/eigen1) by restarted Lanczos (§6)
+ *     or by inverse iteration with CG (§7, Algorithm 2);
+ *   - Recursive Spectral Bisection (§4, Algorithm 1) with floor/ceil splits of
+ *     the part count and proportional element counts.
+ *
+ * Memory.  Every pointer argument may be a device pointer or a host pointer;
+ * the library asks the CUDA runtime which it is.  Host inputs are copied to
+ * the device and host outputs copied back inside the call (the call then
+ * returns only after the copy-back).  The caller owns every buffer it passes;
+ * the library keeps none of them after returning.  The library owns a cached
+ * device workspace that grows as needed and is freed by rsb_release().
+ *
+ * Streams.  `stream` is a cudaStream_t (NULL = legacy default stream).  Work is
+ * issued on that stream; the calls synchronise with it before returning
+ * (convergence decisions and statistics are read back on the host).
+ *
+ * Errors.  Every call returns one of the RSB_* codes below; RSB_OK is 0.
+ * Invalid arguments are rejected with RSB_EINVAL before any device work.
+ * A device error is reported as RSB_ECUDA (the CUDA error string is kept for
+ * rsb_last_error_detail()).  RSB_ENOCONV means some solve hit its iteration
+ * cap; outputs are still written from the best iterate.
+ *
+ * Threading.  Calls are not re-entrant: one call at a time per process.
+ */
+#ifndef RSB_H
+#define RSB_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  RSB_OK = 0,
+  RSB_EINVAL = 1,        /* bad argument or malformed graph                    */
+  RSB_ENOMEM = 2,        /* device allocation failed                           */
+  RSB_ECUDA = 3,         /* CUDA runtime / kernel error                        */
+  RSB_ENOCONV = 4,       /* a Fiedler solve stopped at its iteration cap       */
+  RSB_ETIMEOUT = 5,      /* a bounded device wait gave up                      */
+  RSB_EDISCONNECTED = 6  /* rsb_fiedler: the graph has several components      */
+};
+
+enum { RSB_LANCZOS = 0, RSB_INVERSE = 1 };          /* §6, §7                    */
+enum { RSB_FP64 = 0, RSB_MIXED = 1 };               /* arithmetic of the solves  */
+enum { RSB_DEGEN_NONE = 0, RSB_DEGEN_RESOLVE = 1 }; /* repeated lambda_2 (§9)    */
+
+/*
+ * Symmetric graph in CSR form (the dual graph of §2).
+ *   n        number of vertices (elements), 0 <= n < 2^29
+ *   row_ptr  int64[n + 1], row_ptr[0] = 0, non-decreasing
+ *   col      int32[row_ptr[n]], neighbour indices in [0, n), no self loops;
+ *            the pattern and the weights must be symmetric
+ *   weight   int32[row_ptr[n]], integer weights in 1..7 (the paper's weights
+ *            are 1, 2, 4 shared vertices); NULL means every weight is 1
+ *   gid      int64[n], global element ids used for tie-breaks and start
+ *            vectors, distinct within one graph; NULL means gid = row index
+ */
+typedef struct rsb_csr {
+  int64_t n;
+  const int64_t *row_ptr;
+  const int32_t *col;
+  const int32_t *weight;
+  const int64_t *gid;
+} rsb_csr;
+
+typedef struct rsb_options {
+  int method;            /* RSB_LANCZOS | RSB_INVERSE                              */
+  int precision;         /* RSB_FP64 | RSB_MIXED (FP32 vectors + FP64 polish)      */
+  int krylov_dim;        /* Lanczos steps per cycle, 2..40                         */
+  int max_restarts;      /* Lanczos cycles per solve (paper §8: 50)                */
+  double tol;            /* stop when ||L y - theta y|| <= tol * max weighted degree */
+  double cg_tol;         /* CG stop: ||r|| <= cg_tol * ||b||                        */
+  int cg_maxit;          /* CG iterations per outer step                           */
+  int max_outer;         /* inverse-iteration outer steps                          */
+  uint64_t seed;         /* start-vector seed                                      */
+  int degenerate_policy; /* RSB_DEGEN_NONE | RSB_DEGEN_RESOLVE                     */
+  double cluster_tol;    /* RESOLVE: |lambda_b - lambda_a| <= cluster_tol lambda_a  */
+  double tie_rel;        /* median-split tie window, relative to the value range   */
+  double mixed_tol;      /* MIXED: FP32 stage stops at max(tol, mixed_tol)         */
+  int batched;           /* 1: all subgraphs of a level in one set of launches     */
+  int use_graph;         /* 1: capture each Lanczos cycle / CG block in a CUDA graph */
+  int validate;          /* 1: also check symmetry of the input on the device      */
+} rsb_options;
+
+typedef struct rsb_stats {
+  int levels;                 /* bisection levels run                              */
+  int nonconverged;           /* solves that stopped at their cap                  */
+  int64_t solves;             /* Fiedler solves (units x candidates x precisions)  */
+  int64_t cycles;             /* Lanczos cycles or inverse-iteration outer steps  */
+  int64_t inner;              /* CG iterations (inverse iteration)                 */
+  int64_t elements_bisected;  /* sum over levels and split segments of their size */
+  double lambda_first;        /* lambda_2 of the first split of the first mesh     */
+  double resid_max;           /* largest final ||L y - theta y|| / max degree      */
+  double seconds;             /* wall time of the call, host clock                 */
+  int64_t kernel_launches;    /* kernels issued by the call                        */
+} rsb_stats;
+
+/* Fills *o with the defaults: Lanczos, FP64, krylov_dim 40, max_restarts 50,
+ * tol 1e-10, cg_tol 1e-12, cg_maxit 4000, max_outer 50, RESOLVE,
+ * cluster_tol 0.05, tie_rel 1e-5, mixed_tol 1e-6, batched 1, use_graph 1. */
+void rsb_options_default(rsb_options *o);
+
+/*
+ * Recursive spectral bisection of one graph into nparts parts (§4,
+ * Algorithm 1; sizes per §4: a segment of parts [p0, p1) holds
+ * floor(p1 n / P) - floor(p0 n / P) elements and its left child gets the
+ * floor((p1 - p0) / 2) lower-numbered parts).
+ *   g       the graph (device or host pointers)
+ *   nparts  1 <= nparts <= n
+ *   o       options (NULL = defaults)
+ *   part    int32[n] output, part id of every row in [0, nparts)
+ *   st      optional statistics (host pointer, may be NULL)
+ * Returns RSB_EINVAL for nparts out of range or a malformed graph.
+ */
+int rsb_partition(const rsb_csr *g, int32_t nparts, const rsb_options *o,
+                  int32_t *part, rsb_stats *st, void *stream);
+
+/*
+ * rsb_partition for nmesh independent graphs at once: every bisection level of
+ * every mesh is solved together (one set of launches per level when
+ * o->batched).  gs[m], nparts[m] and parts[m] are the arguments of mesh m
+ * (host arrays of structs/pointers; the pointers inside may be device or
+ * host).  Results equal nmesh separate rsb_partition calls.
+ */
+int rsb_partition_batch(const rsb_csr *gs, int32_t nmesh, const int32_t *nparts,
+                        const rsb_options *o, int32_t *const *parts, rsb_stats *st,
+                        void *stream);
+
+/*
+ * Fiedler pair of a connected graph (§4, Eqs. eigen0/eigen1; §6 or §7).
+ *   lambda2  host double out: the smallest eigenvalue of L on 1-perp
+ *   v        double[n] out: unit Fiedler vector, sign fixed so that the
+ *            smallest gid among |v_i| >= max|v| / 2 has v_i < 0
+ *   resid    host double out (nullable): ||L v - lambda2 v||_2
+ * With several components returns RSB_EDISCONNECTED, lambda2 = 0 and v the
+ * normalised contrast vector of the component holding the smallest gid
+ * against the rest.  n must be >= 2.
+ */
+int rsb_fiedler(const rsb_csr *g, const rsb_options *o, double *lambda2, double *v,
+                double *resid, void *stream);
+
+/*
+ * y = L x with L = D - A of graph g (§4 weighted Laplacian, §5 action), on the
+ * library's sliced-ELL form, in FP64 (x, y double[n]) or FP32 (x, y float[n]).
+ * A building block exposed for testing and bandwidth measurement.
+ */
+int rsb_laplacian_apply(const rsb_csr *g, const double *x, double *y, void *stream);
+int rsb_laplacian_apply_f32(const rsb_csr *g, const float *x, float *y, void *stream);
+
+/*
+ * Times `reps` back-to-back applications of the sliced-ELL Laplacian kernel
+ * (FP64 when f32 == 0, else FP32) on graph g with CUDA events on `stream`;
+ * *ms_per_apply receives the mean device time of one launch and
+ * *useful_bytes the algorithmic bytes of one launch (4 B per stored entry
+ * plus one read of x and one write of y).  Build time is excluded.
+ */
+int rsb_laplacian_bench(const rsb_csr *g, int f32, int reps, double *ms_per_apply,
+                        double *useful_bytes, void *stream);
+
+/* Static description of an error code. */
+const char *rsb_strerror(int code);
+
+/* Detail of the last RSB_ECUDA / RSB_EINVAL error (thread-unsafe). */
+const char *rsb_last_error_detail(void);
+
+/* Frees the cached device workspace (all devices touched by this process). */
+void rsb_release(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RSB_H */

@@ -1,0 +1,330 @@
+// rsb_internal.cuh — shared layout, device helpers and launcher declarations of
+// librsb.  Everything here is private to the library; the public surface is
+// include/rsb.h.
+//
+// Data layout in HBM (one "level" of the bisection recursion):
+//   * All subgraphs ("segments") of a level live in one block-diagonal graph of
+//     N rows; segment s owns the contiguous rows [row0, row0 + n).
+//   * The graph is stored as sliced ELL with slice height 32 (SELL-32): row r
+//     sits in slice r >> 5 at lane r & 31, entry k of the row at
+//     ent[slice_ptr[slice] + 32 k + lane].  An entry packs the column in its
+//     low 29 bits and the integer weight (1..7, 0 = padding) in the top 3 bits,
+//     so one 4-byte coalesced load per entry and warp gives both.  The
+//     diagonal is never stored: the Laplacian action is
+//     y_r = sum_k w_rk (x_r - x_{c_k}) (paper §4, L = D - A).
+//   * Vectors are dense arrays over the level's N rows; a Lanczos basis is m+1
+//     such arrays back to back.
+//   * A "unit" is one Fiedler problem: the rows of a segment, or only the
+//     rows of one of its connected components (masked by component key).
+//   * Kernels run one CTA per "tile": a contiguous row range of one unit, so
+//     every CTA reduces into exactly one unit.  The tiling of a unit depends
+//     only on its row count, which makes every reduction's summation order —
+//     and hence every result — independent of what else is in the batch.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "rsb.h"
+
+#define RSB_BLOCK 256
+#define RSB_WARPS (RSB_BLOCK / 32)
+#define RSB_MAXM 40                       // Krylov steps per cycle
+#define RSB_MAXD 2                        // deflation vectors (cluster dim 3)
+#define RSB_MAXC (1 + RSB_MAXD + RSB_MAXM)  // Gram-Schmidt coefficients
+#define RSB_MAXTILES_PER_UNIT 1024
+#define RSB_COLBITS 29
+#define RSB_COLMASK 0x1FFFFFFFu
+#define RSB_MAXN (1 << RSB_COLBITS)
+
+// unit status
+#define U_ACTIVE 0
+#define U_CONVERGED 1
+#define U_CAPPED 2
+#define U_IDLE 3
+
+// ----------------------------------------------------------------------------
+// per-unit state (device)
+// ----------------------------------------------------------------------------
+struct Unit {
+  // geometry, set by the host
+  int32_t row0, nrows;   // row range of the owning segment in the level
+  int32_t seg;           // owning segment
+  int32_t masked;        // rows belong only when ckey[row] == key
+  uint64_t key;
+  int64_t n;             // rows of the unit
+  int64_t k;             // rows that go left (R7 count inside the unit)
+  int32_t tile0, ntile;  // tiles of this unit
+  int32_t valid;         // the unit exists at this level (n >= 2)
+  // solver state
+  double isn;            // 1 / sqrt(n)
+  double dmax;           // largest weighted degree in the unit
+  double tolabs;         // tol * dmax
+  int32_t m;             // Lanczos steps per cycle for this unit
+  int32_t msteps;        // steps available this cycle (m, or fewer on breakdown)
+  int32_t status;
+  int32_t cycles;
+  int32_t maxcycles;
+  int32_t nd;            // deflation vectors in use
+  int32_t inner;         // CG iterations of the last outer step
+  int32_t cg_done;
+  int64_t inner_total;
+  double theta, resid, ynorm2;
+  double beta0;          // norm of the projected start vector
+  double alpha[RSB_MAXM];
+  double beta[RSB_MAXM + 1];
+  double c1[RSB_MAXC], c2[RSB_MAXC];
+  double t[RSB_MAXM];
+  double cp[1 + RSB_MAXD];
+  // CG scalars (§7): FP64 recurrences in both precisions
+  double rr, cg_alpha, cg_beta, bnorm;
+  double rq, lnorm2;
+  // select / split
+  double vmax, vmin, amax;
+  double sign;
+  double vk, tau;
+  uint64_t sel_prefix;
+  int64_t sel_k, sel_below, sel_eq;
+  int64_t gstar;
+  double gstar_v;
+  int64_t below;
+  int64_t cut[3];
+  double lam[3];         // eigenvalue of each candidate solve
+  double res[3];         // final residual of each candidate solve
+  int32_t best;
+  int32_t ncand;
+  unsigned int cnt;      // last-CTA counter of the segmented reductions
+  int32_t pad1;
+};
+
+struct Tile {
+  int32_t unit;
+  int32_t row0, row1;
+  int32_t pad;
+};
+
+// ----------------------------------------------------------------------------
+// device helpers
+// ----------------------------------------------------------------------------
+#ifdef __CUDACC__
+
+__device__ __forceinline__ uint32_t ent_col(uint32_t e) { return e & RSB_COLMASK; }
+__device__ __forceinline__ uint32_t ent_w(uint32_t e) { return e >> RSB_COLBITS; }
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ double warp_max(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+__device__ __forceinline__ long long warp_sum_ll(long long v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Block sum of one double per thread, deterministic; result valid in thread 0.
+__device__ __forceinline__ double block_sum(double v, double* sm) {
+  v = warp_sum(v);
+  const int w = threadIdx.x >> 5;
+  if ((threadIdx.x & 31) == 0) sm[w] = v;
+  __syncthreads();
+  double s = 0.0;
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int i = 0; i < RSB_WARPS; ++i) s += sm[i];
+  }
+  __syncthreads();
+  return s;
+}
+
+// SplitMix64 (Steele, Lea & Flood 2014): output for state x.
+__device__ __host__ __forceinline__ uint64_t splitmix64(uint64_t x) {
+  uint64_t z = x + 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+// Start-vector entry 2 u - 1, u = top 53 bits of SplitMix64(s_d ^ gid) / 2^53.
+__device__ __forceinline__ double start_value(uint64_t sd, int64_t gid) {
+  const uint64_t h = splitmix64(sd ^ (uint64_t)gid);
+  return (double)(h >> 11) * (1.0 / 9007199254740992.0) * 2.0 - 1.0;
+}
+
+// Unsigned key whose order is the numeric order of doubles.
+__device__ __forceinline__ uint64_t dkey(double v) {
+  const uint64_t b = (uint64_t)__double_as_longlong(v);
+  return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
+}
+__device__ __forceinline__ double dkey_inv(uint64_t k) {
+  const uint64_t b = (k >> 63) ? (k & 0x7FFFFFFFFFFFFFFFull) : ~k;
+  return __longlong_as_double((long long)b);
+}
+
+// Row membership in a unit.
+__device__ __forceinline__ bool unit_has(const Unit& u, const uint64_t* ckey, int r) {
+  return !u.masked || ckey[r] == u.key;
+}
+
+// Compensated accumulator: FP64 plain, FP32 Kahan (paper-independent
+// precision scheme: FP32 terms, compensated FP32 sums, FP64 across threads).
+template <typename V> struct Acc;
+template <> struct Acc<double> {
+  double s = 0.0;
+  __device__ __forceinline__ void add(double x) { s += x; }
+  __device__ __forceinline__ double get() const { return s; }
+};
+template <> struct Acc<float> {
+  float s = 0.f, c = 0.f;
+  __device__ __forceinline__ void add(float x) {
+    const float y = __fsub_rn(x, c);
+    const float t = __fadd_rn(s, y);
+    c = __fsub_rn(__fsub_rn(t, s), y);
+    s = t;
+  }
+  __device__ __forceinline__ double get() const { return (double)s - (double)c; }
+};
+
+// Last-CTA election of a unit's segmented reduction: every CTA of the unit
+// has stored its partials; the CTA that arrives last reduces them in tile
+// order (so the result does not depend on which CTA is last) and resets the
+// counter for the next kernel.  No CTA waits on another.
+__device__ __forceinline__ bool last_cta(unsigned int* cnt, int ntile) {
+  __shared__ int am_last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const unsigned prev = atomicAdd(cnt, 1u);
+    am_last = (prev == (unsigned)(ntile - 1));
+    if (am_last) *cnt = 0u;
+  }
+  __syncthreads();
+  if (am_last) __threadfence();
+  return am_last != 0;
+}
+
+// out[c] = sum_t partials[c * stride + t0 + t], t in [0, nt), c in [0, nc);
+// fixed order (lane-strided then butterfly), executed by the whole CTA.
+__device__ __forceinline__ void final_reduce(const double* partials, long long stride, int t0,
+                                             int nt, int nc, double* out) {
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int c = w; c < nc; c += RSB_WARPS) {
+    double s = 0.0;
+    for (int t = lane; t < nt; t += 32) s += __ldcg(partials + (long long)c * stride + t0 + t);
+    s = warp_sum(s);
+    if (lane == 0) out[c] = s;
+  }
+  __syncthreads();
+}
+
+#endif  // __CUDACC__
+
+// ----------------------------------------------------------------------------
+// host-side workspace
+// ----------------------------------------------------------------------------
+struct DevBuf {
+  void* p = nullptr;
+  size_t cap = 0;
+};
+
+// Level-resident graph.
+struct LevelGraph {
+  int32_t n = 0;
+  int64_t nslices = 0;
+  int64_t* slice_ptr = nullptr;  // nslices + 1
+  uint32_t* ent = nullptr;       // packed entries
+  int32_t* deg = nullptr;        // weighted degree per row
+  int64_t* gid = nullptr;
+  int64_t* home = nullptr;       // index into the caller's (concatenated) output
+  int32_t* row_seg = nullptr;
+  int64_t nent = 0;
+};
+
+struct SegHost {
+  int64_t row0, n;
+  int32_t p0, p1, mesh;
+  int64_t nleft;
+};
+
+// Error helpers (host)
+int rsb_set_cuda_error(cudaError_t e, const char* where);
+int rsb_set_error(int code, const std::string& what);
+void rsb_count_launch(int k = 1);
+
+#define RSB_CK(call)                                              \
+  do {                                                            \
+    cudaError_t e__ = (call);                                     \
+    if (e__ != cudaSuccess) return rsb_set_cuda_error(e__, #call); \
+  } while (0)
+#define RSB_CKL(where)                                                         \
+  do {                                                                         \
+    rsb_count_launch();                                                        \
+    cudaError_t e__ = cudaGetLastError();                                      \
+    if (e__ != cudaSuccess) return rsb_set_cuda_error(e__, where);             \
+  } while (0)
+
+// Grow-only device buffer.
+int devbuf_reserve(DevBuf& b, size_t bytes);
+template <typename T>
+static inline T* dptr(DevBuf& b) {
+  return reinterpret_cast<T*>(b.p);
+}
+
+// ----------------------------------------------------------------------------
+// launchers (graph.cu); the others are declared where they are used
+// ----------------------------------------------------------------------------
+int launch_validate(const int64_t* row_ptr, const int32_t* col, const int32_t* wt, int64_t n,
+                    int symmetric, int* flag, cudaStream_t s);
+int launch_row_lengths(const int64_t* row_ptr, int64_t n, int32_t* len, cudaStream_t s);
+int launch_slice_widths(const int32_t* len, int64_t n, int64_t* slice_sz, cudaStream_t s);
+int launch_fill_sell(const int64_t* row_ptr, const int32_t* col, const int32_t* wt,
+                     const int64_t* gid_in, int64_t n, int64_t row_off, int64_t home_off,
+                     int32_t seg, const int64_t* slice_ptr, uint32_t* ent, int32_t* deg,
+                     int64_t* gid, int64_t* home, int32_t* row_seg, cudaStream_t s);
+int launch_scan_i64(const int64_t* in, int64_t* out_excl, int64_t n, void* tmp, size_t tmp_bytes,
+                    cudaStream_t s);
+size_t scan_tmp_bytes(int64_t n);
+int launch_spmv_f64(const LevelGraph& G, const double* x, double* y, cudaStream_t s);
+int launch_spmv_f32(const LevelGraph& G, const float* x, float* y, cudaStream_t s);
+int launch_cc(const LevelGraph& G, int32_t* parent, uint64_t* ckey, int* flag, cudaStream_t s);
+int launch_comp_count(const LevelGraph& G, const int32_t* parent, int32_t* seg_ncomp,
+                      cudaStream_t s);
+int launch_compact(const LevelGraph& G, LevelGraph& H, const uint8_t* side,
+                   const int64_t* seg_row0_old, const int64_t* seg_nleft,
+                   const int32_t* seg_child0, int32_t nseg, int64_t* newpos, int64_t* tmp64,
+                   int32_t* len, int64_t* slice_sz, void* scan_tmp, size_t scan_tmp_bytes,
+                   DevBuf& ent_buf, cudaStream_t s);
+int launch_write_parts(const LevelGraph& G, const int32_t* seg_p0, int32_t* part_concat,
+                       cudaStream_t s);
+int launch_degree_max(const LevelGraph& G, const Tile* tiles, int ntiles, Unit* units,
+                      const uint64_t* ckey, double* partials, cudaStream_t s);
+int launch_split_assign(const LevelGraph& G, const Tile* tiles, int ntiles, Unit* units,
+                        const uint64_t* ckey, const double* v, uint8_t* side, int cand,
+                        cudaStream_t s);
+
+// solver buffers of one precision (V = double or float)
+struct SolveBufs {
+  void* Q = nullptr;       // M x N basis vectors
+  void* W0 = nullptr;      // work vectors
+  void* W1 = nullptr;
+  void* Y = nullptr;
+  void* X = nullptr;       // CG
+  void* R = nullptr;
+  void* P = nullptr;
+  void* AP = nullptr;
+  const double* D[RSB_MAXD] = {nullptr, nullptr};  // deflation vectors (FP64)
+  double* partials = nullptr;
+  int* n_active = nullptr;       // device: units still iterating
+  int* n_cg = nullptr;           // device: units whose CG still runs
+  long long* stat_cycles = nullptr;
+  int* h_active = nullptr;       // pinned host word for read-backs
+  int64_t N = 0;
+};

@@ -1,0 +1,1194 @@
+// solver.cu — Fiedler solvers of librsb, batched over all units of a level.
+//
+// Lanczos with restarts (paper §6): per step
+//   A: w = L q_j - beta_j q_{j-1}, fused with the first Gram-Schmidt pass's
+//      dot products against [1/sqrt(n), deflation vectors, q_0..q_j]
+//      (alpha_j is the coefficient on q_j),
+//   B: w -= basis * c1, fused with the second pass's dot products,
+//   C: w -= basis * c2, fused with ||w||^2 -> beta_{j+1}.
+// q_{j+1} = w / beta_{j+1} is materialised by the next step's A, which gathers
+// the unnormalised w and scales.  After the cycle: the smallest eigenpair of
+// the tridiagonal T (one warp per unit, FP64), the Ritz vector y = Q t, the
+// true residual ||L y - theta y||, and an explicit restart from y projected
+// against the fixed basis (two classical Gram-Schmidt passes).
+//
+// Inverse iteration (paper §7, Algorithm 2): the right-hand side b is the
+// projected, normalised previous iterate; L x = b is solved by CG from x0 = 0
+// with r projected against the fixed basis every step; the Rayleigh quotient
+// and residual of x decide the stop (also when CG returned after a single
+// iteration, §7).
+//
+// Precision: V = double (plain FP64) or V = float (vectors, SpMV and updates
+// in FP32; per-thread Kahan sums in FP32; CTA and cross-CTA sums, the
+// Gram-Schmidt coefficients, T, and the CG alpha/beta recurrences in FP64).
+#include <algorithm>
+#include <cfloat>
+
+#include "rsb_internal.cuh"
+
+template <typename V>
+struct LzArgs {
+  const int64_t* slice_ptr;
+  const uint32_t* ent;
+  const int64_t* gid;
+  const Tile* tiles;
+  Unit* units;
+  const uint64_t* ckey;
+  V* Q;
+  long long N;
+  V* W0;
+  V* W1;
+  V* Y;
+  V* X;
+  V* R;
+  V* P;
+  V* AP;
+  const double* D0;
+  const double* D1;
+  double* partials;
+  long long stride;
+  int* n_active;
+  long long* stat_cycles;
+};
+
+template <typename V>
+__device__ __forceinline__ V spmv_row(const int64_t* __restrict__ slice_ptr,
+                                      const uint32_t* __restrict__ ent, const V* __restrict__ x,
+                                      int r, V xr) {
+  const int64_t base = slice_ptr[r >> 5];
+  const int width = (int)((slice_ptr[(r >> 5) + 1] - base) >> 5);
+  const uint32_t* e = ent + base + (r & 31);
+  V acc = V(0);
+#pragma unroll 4
+  for (int k = 0; k < width; ++k) {
+    const uint32_t p = __ldg(e + 32 * k);
+    acc += V(ent_w(p)) * (xr - x[ent_col(p)]);
+  }
+  return acc;
+}
+
+// Basis vector c of the Gram-Schmidt set [u0, D_0.., q_0..] at row r.
+// u0 = 1/sqrt(n) on unit rows; callers multiply by isn themselves where it
+// matters (its dot is taken as a plain sum).
+template <typename V>
+__device__ __forceinline__ V basis_at(const LzArgs<V>& a, int nd, int c, int r) {
+  if (c == 0) return V(1);
+  if (c <= nd) return V((c == 1 ? a.D0 : a.D1)[r]);
+  return a.Q[(long long)(c - 1 - nd) * a.N + r];
+}
+
+// Warp-per-coefficient dot products of the basis with the 256 values in ws
+// (rows base..base+255 of the tile); coefficient c lives in warp c % 8.
+#define MAXCW ((RSB_MAXC + RSB_WARPS - 1) / RSB_WARPS)
+template <typename V>
+__device__ __forceinline__ void tile_dots(const LzArgs<V>& a, int nd, int c0, int nc, int base,
+                                          int rowend, const V* ws, Acc<V> (&acc)[MAXCW]) {
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+  for (int i = 0; i < MAXCW; ++i) {
+    const int c = w + RSB_WARPS * i;
+    if (c >= nc) break;
+    const int cc = c0 + c;
+#pragma unroll 4
+    for (int q = 0; q < 8; ++q) {
+      const int row = base + lane + 32 * q;
+      if (row < rowend) acc[i].add(basis_at(a, nd, cc, row) * ws[lane + 32 * q]);
+    }
+  }
+}
+
+template <typename V>
+__device__ __forceinline__ void store_dots(const LzArgs<V>& a, int nc, Acc<V> (&acc)[MAXCW]) {
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+  for (int i = 0; i < MAXCW; ++i) {
+    const int c = w + RSB_WARPS * i;
+    if (c >= nc) break;
+    const double s = warp_sum(acc[i].get());
+    if (lane == 0) a.partials[(long long)c * a.stride + blockIdx.x] = s;
+  }
+}
+
+// ----------------------------------------------------------------------------
+// Lanczos step kernels
+// ----------------------------------------------------------------------------
+template <typename V>
+__global__ void __launch_bounds__(RSB_BLOCK) k_lz_a(LzArgs<V> a, int j) {
+  __shared__ V ws[RSB_BLOCK];
+  __shared__ double out[RSB_MAXC];
+  const Tile t = a.tiles[blockIdx.x];
+  Unit& u = a.units[t.unit];
+  if (u.status != U_ACTIVE || j >= u.msteps) return;
+  const V* src = (j & 1) ? a.W1 : a.W0;
+  V* dst = (j & 1) ? a.W0 : a.W1;
+  V* qj = a.Q + (long long)j * a.N;
+  const V* qjm = j ? a.Q + (long long)(j - 1) * a.N : nullptr;
+  const double sc = 1.0 / (j == 0 ? u.beta0 : u.beta[j]);
+  const V s = V(sc);
+  const V bj = V(j ? u.beta[j] : 0.0);
+  const bool last = (j == u.m - 1);
+  const int nd = u.nd;
+  const int nc = last ? 1 : (2 + nd + j);
+  const int c0 = last ? (1 + nd + j) : 0;
+  Acc<V> acc[MAXCW];
+  for (int base = t.row0; base < t.row1; base += RSB_BLOCK) {
+    const int r = base + threadIdx.x;
+    V w = V(0);
+    if (r < t.row1) {
+      const V xr = src[r];
+      w = s * spmv_row<V>(a.slice_ptr, a.ent, src, r, xr);
+      if (j) w -= bj * qjm[r];
+      qj[r] = s * xr;
+      if (!last) dst[r] = w;
+    }
+    ws[threadIdx.x] = w;
+    __syncthreads();
+    tile_dots<V>(a, nd, c0, nc, base, t.row1, ws, acc);
+    __syncthreads();
+  }
+  store_dots<V>(a, nc, acc);
+  if (last_cta(&u.cnt, u.ntile)) {
+    final_reduce(a.partials, a.stride, u.tile0, u.ntile, nc, out);
+    if (threadIdx.x == 0) {
+      if (last) {
+        u.alpha[j] = out[0];
+      } else {
+        u.c1[0] = out[0] * u.isn;
+        for (int c = 1; c < nc; ++c) u.c1[c] = out[c];
+        u.alpha[j] = out[nc - 1];
+      }
+    }
+  }
+}
+
+// w -= sum_c coef[c] basis_c at row r (u0 only on unit rows)
+template <typename V>
+__device__ __forceinline__ V gs_update(const LzArgs<V>& a, const Unit& u, const double* coef,
+                                       int nd, int nq, int r, V w) {
+  if (unit_has(u, a.ckey, r)) w -= V(coef[0] * u.isn);
+  if (nd > 0) w -= V(coef[1]) * V(a.D0[r]);
+  if (nd > 1) w -= V(coef[2]) * V(a.D1[r]);
+  const V* q = a.Q + r;
+  const double* cq = coef + 1 + nd;
+#pragma unroll 4
+  for (int k = 0; k < nq; ++k) w -= V(cq[k]) * q[(long long)k * a.N];
+  return w;
+}
+
+template <typename V>
+__global__ void __launch_bounds__(RSB_BLOCK) k_lz_b(LzArgs<V> a, int j) {
+  __shared__ V ws[RSB_BLOCK];
+  __shared__ double out[RSB_MAXC];
+  const Tile t = a.tiles[blockIdx.x];
+  Unit& u = a.units[t.unit];
+  if (u.status != U_ACTIVE || j >= u.msteps || j == u.m - 1) return;
+  V* w_ = (j & 1) ? a.W0 : a.W1;
+  const int nd = u.nd;
+  const int nc = 2 + nd + j;
+  Acc<V> acc[MAXCW];
+  for (int base = t.row0; base < t.row1; base += RSB_BLOCK) {
+    const int r = base + threadIdx.x;
+    V w = V(0);
+    if (r < t.row1) {
+      w = gs_update<V>(a, u, u.c1, nd, j + 1, r, w_[r]);
+      w_[r] = w;
+    }
+    ws[threadIdx.x] = w;
+    __syncthreads();
+    tile_dots<V>(a, nd, 0, nc, base, t.row1, ws, acc);
+    __syncthreads();
+  }
+  store_dots<V>(a, nc, acc);
+  if (last_cta(&u.cnt, u.ntile)) {
+    final_reduce(a.partials, a.stride, u.tile0, u.ntile, nc, out);
+    if (threadIdx.x == 0) {
+      u.c2[0] = out[0] * u.isn;
+      for (int c = 1; c < nc; ++c) u.c2[c] = out[c];
+    }
+  }
+}
+
+template <typename V>
+__global__ void __launch_bounds__(RSB_BLOCK) k_lz_c(LzArgs<V> a, int j, double breakdown) {
+  __shared__ double sm[RSB_WARPS];
+  __shared__ double out[1];
+  const Tile t = a.tiles[blockIdx.x];
+  Unit& u = a.units[t.unit];
+  if (u.status != U_ACTIVE || j >= u.msteps || j == u.m - 1) return;
+  V* w_ = (j & 1) ? a.W0 : a.W1;
+  const int nd = u.nd;
+  Acc<V> acc;
+  for (int r = t.row0 + threadIdx.x; r < t.row1; r += RSB_BLOCK) {
+    const V w = gs_update<V>(a, u, u.c2, nd, j + 1, r, w_[r]);
+    w_[r] = w;
+    acc.add(w * w);
+  }
+  const double s = block_sum(acc.get(), sm);
+  if (threadIdx.x == 0) a.partials[blockIdx.x] = s;
+  if (last_cta(&u.cnt, u.ntile)) {
+    final_reduce(a.partials, a.stride, u.tile0, u.ntile, 1, out);
+    if (threadIdx.x == 0) {
+      const double b = sqrt(out[0]);
+      if (b <= breakdown * u.dmax) u.msteps = j + 1;  // invariant subspace: cycle ends
+      else u.beta[j + 1] = b;
+    }
+  }
+}
+
+// ----------------------------------------------------------------------------
+// smallest eigenpair of the symmetric tridiagonal T_K (one warp per unit)
+// ----------------------------------------------------------------------------
+// Eigenvalue: Sturm-count multisection (32 shifts per round); eigenvector:
+// inverse iteration with Gaussian elimination with partial pivoting on the
+// tridiagonal T - theta I.
+__device__ int sturm_count(const double* al, const double* be, int K, double sig, double pivmin) {
+  int cnt = 0;
+  double d = al[0] - sig;
+  if (fabs(d) < pivmin) d = -pivmin;
+  if (d < 0) ++cnt;
+  for (int k = 1; k < K; ++k) {
+    d = al[k] - sig - be[k] * be[k] / d;
+    if (fabs(d) < pivmin) d = -pivmin;
+    if (d < 0) ++cnt;
+  }
+  return cnt;
+}
+
+__device__ void tridiag_solve_pivot(const double* al, const double* be, int K, double theta,
+                                    double pert, double* x) {
+  double d[RSB_MAXM], du[RSB_MAXM], dl[RSB_MAXM], b[RSB_MAXM];
+  for (int k = 0; k < K; ++k) {
+    d[k] = al[k] - theta;
+    du[k] = (k + 1 < K) ? be[k + 1] : 0.0;
+    dl[k] = (k + 1 < K) ? be[k + 1] : 0.0;
+    b[k] = x[k];
+  }
+  double du2[RSB_MAXM];
+  for (int k = 0; k < K; ++k) du2[k] = 0.0;
+  for (int k = 0; k + 1 < K; ++k) {
+    if (fabs(d[k]) >= fabs(dl[k])) {
+      if (d[k] == 0.0) d[k] = pert;
+      const double f = dl[k] / d[k];
+      d[k + 1] -= f * du[k];
+      b[k + 1] -= f * b[k];
+    } else {
+      const double f = d[k] / dl[k];
+      d[k] = dl[k];
+      const double tmp = d[k + 1];
+      d[k + 1] = du[k] - f * tmp;
+      if (k + 2 < K) {
+        du2[k] = du[k + 1];
+        du[k + 1] = -f * du2[k];
+      }
+      du[k] = tmp;
+      const double tb = b[k];
+      b[k] = b[k + 1];
+      b[k + 1] = tb - f * b[k + 1];
+    }
+  }
+  if (d[K - 1] == 0.0) d[K - 1] = pert;
+  x[K - 1] = b[K - 1] / d[K - 1];
+  if (K >= 2) x[K - 2] = (b[K - 2] - du[K - 2] * x[K - 1]) / d[K - 2];
+  for (int k = K - 3; k >= 0; --k) x[k] = (b[k] - du[k] * x[k + 1] - du2[k] * x[k + 2]) / d[k];
+}
+
+__global__ void k_lz_tridiag(Unit* units, int nunits) {
+  const int ui = blockIdx.x;
+  if (ui >= nunits) return;
+  Unit& u = units[ui];
+  if (u.status != U_ACTIVE) return;
+  const int lane = threadIdx.x;
+  const int K = u.msteps;
+  const double* al = u.alpha;
+  const double* be = u.beta;  // be[k] couples rows k-1 and k
+  double lo = 1e300, hi = -1e300, bmax = 0.0;
+  for (int k = 0; k < K; ++k) {
+    const double r = (k > 0 ? fabs(be[k]) : 0.0) + (k + 1 < K ? fabs(be[k + 1]) : 0.0);
+    lo = fmin(lo, al[k] - r);
+    hi = fmax(hi, al[k] + r);
+    if (k > 0) bmax = fmax(bmax, fabs(be[k]));
+  }
+  const double tnorm = fmax(fabs(lo), fabs(hi));
+  const double pivmin = DBL_MIN * fmax(1.0, bmax * bmax);
+  // multisection for the smallest eigenvalue: invariant count(lo) = 0 <= count(hi)
+  for (int it = 0; it < 40; ++it) {
+    if (hi - lo <= 2.0 * DBL_EPSILON * fmax(fabs(lo), fabs(hi)) + pivmin) break;
+    const double step = (hi - lo) / 33.0;
+    const double sig = lo + step * (lane + 1);
+    const int c = sturm_count(al, be, K, sig, pivmin);
+    const unsigned m = __ballot_sync(0xffffffffu, c >= 1);
+    const int first = m ? __ffs(m) - 1 : 32;
+    const double nhi = first < 32 ? lo + step * (first + 1) : hi;
+    const double nlo = first > 0 ? lo + step * first : lo;
+    lo = nlo;
+    hi = nhi;
+  }
+  const double theta = 0.5 * (lo + hi);
+  if (lane == 0) {
+    double x[RSB_MAXM];
+    for (int k = 0; k < K; ++k) x[k] = 1.0;
+    const double pert = DBL_EPSILON * fmax(tnorm, DBL_MIN);
+    for (int it = 0; it < 3; ++it) {
+      tridiag_solve_pivot(al, be, K, theta, pert, x);
+      double nrm = 0.0;
+      for (int k = 0; k < K; ++k) nrm += x[k] * x[k];
+      nrm = 1.0 / sqrt(nrm);
+      for (int k = 0; k < K; ++k) x[k] *= nrm;
+    }
+    for (int k = 0; k < K; ++k) u.t[k] = x[k];
+    u.theta = theta;
+  }
+}
+
+// ----------------------------------------------------------------------------
+// Ritz vector, residual, restart
+// ----------------------------------------------------------------------------
+template <typename V>
+__global__ void __launch_bounds__(RSB_BLOCK) k_lz_ritz(LzArgs<V> a) {
+  const Tile t = a.tiles[blockIdx.x];
+  const Unit& u = a.units[t.unit];
+  if (u.status != U_ACTIVE) return;
+  const int K = u.msteps;
+  for (int r = t.row0 + threadIdx.x; r < t.row1; r += RSB_BLOCK) {
+    V y = V(0);
+    const V* q = a.Q + r;
+#pragma unroll 4
+    for (int k = 0; k < K; ++k) y += V(u.t[k]) * q[(long long)k * a.N];
+    a.Y[r] = y;
+  }
+}
+
+// Residual of y (src) with theta, plus the projection dots of y against the
+// fixed basis.  mode 0: Lanczos cycle end (decides convergence); mode 1: the
+// start vector only (no residual).
+template <typename V>
+__global__ void __launch_bounds__(RSB_BLOCK) k_lz_resid(LzArgs<V> a, const V* __restrict__ y,
+                                                        int mode) {
+  __shared__ double sm[RSB_WARPS];
+  __shared__ double out[3 + RSB_MAXD];
+  const Tile t = a.tiles[blockIdx.x];
+  Unit& u = a.units[t.unit];
+  if (u.status != U_ACTIVE) return;
+  const int nd = u.nd;
+  const V th = V(u.theta);
+  Acc<V> r2, y2, ys, d0, d1;
+  for (int r = t.row0 + threadIdx.x; r < t.row1; r += RSB_BLOCK) {
+    const V yr = y[r];
+    if (mode == 0) {
+      const V res = spmv_row<V>(a.slice_ptr, a.ent, y, r, yr) - th * yr;
+      r2.add(res * res);
+    }
+    y2.add(yr * yr);
+    ys.add(yr);
+    if (nd > 0) d0.add(V(a.D0[r]) * yr);
+    if (nd > 1) d1.add(V(a.D1[r]) * yr);
+  }
+  double v[5] = {r2.get(), y2.get(), ys.get(), d0.get(), d1.get()};
+  const int nv = 3 + nd;
+  for (int c = 0; c < nv; ++c) {
+    const double s = block_sum(v[c], sm);
+    if (threadIdx.x == 0) a.partials[(long long)c * a.stride + blockIdx.x] = s;
+  }
+  if (last_cta(&u.cnt, u.ntile)) {
+    final_reduce(a.partials, a.stride, u.tile0, u.ntile, nv, out);
+    if (threadIdx.x == 0) {
+      u.ynorm2 = out[1];
+      u.cp[0] = out[2] * u.isn;
+      for (int l = 0; l < nd; ++l) u.cp[1 + l] = out[3 + l];
+      if (mode == 0) {
+        u.resid = sqrt(out[0] / out[1]);
+        u.cycles += 1;
+        atomicAdd((unsigned long long*)a.stat_cycles, 1ull);
+        int st = U_ACTIVE;
+        if (u.resid <= u.tolabs) st = U_CONVERGED;
+        else if (u.cycles >= u.maxcycles) st = U_CAPPED;
+        if (st != U_ACTIVE) {
+          u.status = st;
+          atomicSub(a.n_active, 1);
+        }
+      }
+    }
+  }
+}
+
+// y -= B cp (in place); dots of the result against B -> c2.
+template <typename V>
+__global__ void __launch_bounds__(RSB_BLOCK) k_proj2(LzArgs<V> a, V* __restrict__ y) {
+  __shared__ double sm[RSB_WARPS];
+  __shared__ double out[1 + RSB_MAXD];
+  const Tile t = a.tiles[blockIdx.x];
+  Unit& u = a.units[t.unit];
+  if (u.status != U_ACTIVE) return;
+  const int nd = u.nd;
+  Acc<V> ys, d0, d1;
+  for (int r = t.row0 + threadIdx.x; r < t.row1; r += RSB_BLOCK) {
+    V v = y[r];
+    if (unit_has(u, a.ckey, r)) v -= V(u.cp[0] * u.isn);
+    if (nd > 0) v -= V(u.cp[1]) * V(a.D0[r]);
+    if (nd > 1) v -= V(u.cp[2]) * V(a.D1[r]);
+    y[r] = v;
+    ys.add(v);
+    if (nd > 0) d0.add(V(a.D0[r]) * v);
+    if (nd > 1) d1.add(V(a.D1[r]) * v);
+  }
+  double v[3] = {ys.get(), d0.get(), d1.get()};
+  const int nv = 1 + nd;
+  for (int c = 0; c < nv; ++c) {
+    const double s = block_sum(v[c], sm);
+    if (threadIdx.x == 0) a.partials[(long long)c * a.stride + blockIdx.x] = s;
+  }
+  if (last_cta(&u.cnt, u.ntile)) {
+    final_reduce(a.partials, a.stride, u.tile0, u.ntile, nv, out);
+    if (threadIdx.x == 0) {
+      u.c2[0] = out[0] * u.isn;
+      for (int l = 0; l < nd; ++l) u.c2[1 + l] = out[1 + l];
+    }
+  }
+}
+
+// w0 = y - B c2 (second pass), beta0 = ||w0||; new cycle starts.
+template <typename V>
+__global__ void __launch_bounds__(RSB_BLOCK) k_proj3(LzArgs<V> a, const V* __restrict__ y) {
+  __shared__ double sm[RSB_WARPS];
+  __shared__ double out[1];
+  const Tile t = a.tiles[blockIdx.x];
+  Unit& u = a.units[t.unit];
+  if (u.status != U_ACTIVE) return;
+  const int nd = u.nd;
+  Acc<V> acc;
+  for (int r = t.row0 + threadIdx.x; r < t.row1; r += RSB_BLOCK) {
+    V v = y[r];
+    if (unit_has(u, a.ckey, r)) v -= V(u.c2[0] * u.isn);
+    if (nd > 0) v -= V(u.c2[1]) * V(a.D0[r]);
+    if (nd > 1) v -= V(u.c2[2]) * V(a.D1[r]);
+    a.W0[r] = v;
+    acc.add(v * v);
+  }
+  const double s = block_sum(acc.get(), sm);
+  if (threadIdx.x == 0) a.partials[blockIdx.x] = s;
+  if (last_cta(&u.cnt, u.ntile)) {
+    final_reduce(a.partials, a.stride, u.tile0, u.ntile, 1, out);
+    if (threadIdx.x == 0) {
+      u.beta0 = sqrt(out[0]);
+      u.msteps = u.m;
+    }
+  }
+}
+
+// Start vector into Y: hash of gid on unit rows (or a given vector), 0 elsewhere.
+template <typename V>
+__global__ void __launch_bounds__(RSB_BLOCK) k_start(LzArgs<V> a, uint64_t sd, const double* from64,
+                                                     const float* from32) {
+  const Tile t = a.tiles[blockIdx.x];
+  const Unit& u = a.units[t.unit];
+  if (u.status != U_ACTIVE) return;
+  for (int r = t.row0 + threadIdx.x; r < t.row1; r += RSB_BLOCK) {
+    V v = V(0);
+    if (unit_has(u, a.ckey, r)) {
+      if (from64) v = V(from64[r]);
+      else if (from32) v = V(from32[r]);
+      else v = V(start_value(sd, a.gid[r]));
+    }
+    a.Y[r] = v;
+  }
+}
+
+// ----------------------------------------------------------------------------
+// solve set-up per unit
+// ----------------------------------------------------------------------------
+// mode: number of deflation vectors nd (0, 1, 2).  A unit joins the solve when
+// it is valid, its space orthogonal to 1 and the deflation vectors is not
+// empty, and (nd > 0) it found a cluster of size nd so far.
+__global__ void k_solve_init(Unit* units, int nunits, int nd, int krylov, int maxcycles, double tol,
+                             int require_cluster, int* n_active) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nunits) return;
+  Unit& u = units[i];
+  u.status = U_IDLE;
+  if (!u.valid) return;
+  const long long dim = u.n - 1 - nd;
+  if (dim <= 0) return;
+  if (require_cluster && u.ncand != nd) return;
+  u.nd = nd;
+  u.m = (int)min((long long)krylov, dim);
+  u.msteps = u.m;
+  u.cycles = 0;
+  u.maxcycles = maxcycles;
+  u.tolabs = tol * u.dmax;
+  u.inner = 0;
+  u.inner_total = 0;
+  u.cg_done = 0;
+  u.status = U_ACTIVE;
+  atomicAdd(n_active, 1);
+}
+
+// ----------------------------------------------------------------------------
+// host drivers
+// ----------------------------------------------------------------------------
+template <typename V>
+static LzArgs<V> make_args(const LevelGraph& G, const Tile* tiles, int ntiles, Unit* units,
+                           const uint64_t* ckey, SolveBufs& B) {
+  LzArgs<V> a;
+  a.slice_ptr = G.slice_ptr;
+  a.ent = G.ent;
+  a.gid = G.gid;
+  a.tiles = tiles;
+  a.units = units;
+  a.ckey = ckey;
+  a.Q = (V*)B.Q;
+  a.N = B.N;
+  a.W0 = (V*)B.W0;
+  a.W1 = (V*)B.W1;
+  a.Y = (V*)B.Y;
+  a.X = (V*)B.X;
+  a.R = (V*)B.R;
+  a.P = (V*)B.P;
+  a.AP = (V*)B.AP;
+  a.D0 = B.D[0];
+  a.D1 = B.D[1];
+  a.partials = B.partials;
+  a.stride = ntiles;
+  a.n_active = B.n_active;
+  a.stat_cycles = B.stat_cycles;
+  return a;
+}
+
+int solver_setup(Unit* units, int nunits, int nd, int krylov, int maxcycles, double tol,
+                 int require_cluster, SolveBufs& B, cudaStream_t s) {
+  RSB_CK(cudaMemsetAsync(B.n_active, 0, sizeof(int), s));
+  k_solve_init<<<(nunits + 127) / 128, 128, 0, s>>>(units, nunits, nd, krylov, maxcycles, tol,
+                                                    require_cluster, B.n_active);
+  RSB_CKL("k_solve_init");
+  return RSB_OK;
+}
+
+static int read_active(SolveBufs& B, cudaStream_t s, int* out) {
+  RSB_CK(cudaMemcpyAsync(B.h_active, B.n_active, sizeof(int), cudaMemcpyDeviceToHost, s));
+  RSB_CK(cudaStreamSynchronize(s));
+  *out = *B.h_active;
+  return RSB_OK;
+}
+
+template <typename V>
+static int lz_start(LzArgs<V>& a, int ntiles, uint64_t sd, const double* from64,
+                    const float* from32, cudaStream_t s) {
+  k_start<V><<<ntiles, RSB_BLOCK, 0, s>>>(a, sd, from64, from32);
+  RSB_CKL("k_start");
+  k_lz_resid<V><<<ntiles, RSB_BLOCK, 0, s>>>(a, a.Y, 1);
+  RSB_CKL("k_lz_resid(start)");
+  k_proj2<V><<<ntiles, RSB_BLOCK, 0, s>>>(a, a.Y);
+  RSB_CKL("k_proj2");
+  k_proj3<V><<<ntiles, RSB_BLOCK, 0, s>>>(a, a.Y);
+  RSB_CKL("k_proj3");
+  return RSB_OK;
+}
+
+template <typename V>
+static int lz_cycle(LzArgs<V>& a, int ntiles, int nunits, int M, double breakdown, cudaStream_t s) {
+  for (int j = 0; j < M; ++j) {
+    k_lz_a<V><<<ntiles, RSB_BLOCK, 0, s>>>(a, j);
+    RSB_CKL("k_lz_a");
+    if (j + 1 < M) {
+      k_lz_b<V><<<ntiles, RSB_BLOCK, 0, s>>>(a, j);
+      RSB_CKL("k_lz_b");
+      k_lz_c<V><<<ntiles, RSB_BLOCK, 0, s>>>(a, j, breakdown);
+      RSB_CKL("k_lz_c");
+    }
+  }
+  k_lz_tridiag<<<nunits, 32, 0, s>>>(a.units, nunits);
+  RSB_CKL("k_lz_tridiag");
+  k_lz_ritz<V><<<ntiles, RSB_BLOCK, 0, s>>>(a);
+  RSB_CKL("k_lz_ritz");
+  k_lz_resid<V><<<ntiles, RSB_BLOCK, 0, s>>>(a, a.Y, 0);
+  RSB_CKL("k_lz_resid");
+  k_proj2<V><<<ntiles, RSB_BLOCK, 0, s>>>(a, a.Y);
+  RSB_CKL("k_proj2");
+  k_proj3<V><<<ntiles, RSB_BLOCK, 0, s>>>(a, a.Y);
+  RSB_CKL("k_proj3");
+  return RSB_OK;
+}
+
+// Runs Lanczos cycles until every participating unit converged or hit its cap.
+// The start is the gid hash with seed sd, or from64 / from32 when given.
+template <typename V>
+static int lanczos_run(const LevelGraph& G, const Tile* tiles, int ntiles, Unit* units, int nunits,
+                       const uint64_t* ckey, SolveBufs& B, int M, uint64_t sd,
+                       const double* from64, const float* from32, int use_graph,
+                       cudaStream_t s) {
+  LzArgs<V> a = make_args<V>(G, tiles, ntiles, units, ckey, B);
+  int active = 0;
+  int rc = read_active(B, s, &active);
+  if (rc || active == 0) return rc;
+  rc = lz_start<V>(a, ntiles, sd, from64, from32, s);
+  if (rc) return rc;
+  const double breakdown = 1e-14;
+  cudaGraphExec_t exec = nullptr;
+  if (use_graph) {
+    cudaGraph_t graph = nullptr;
+    RSB_CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+    rc = lz_cycle<V>(a, ntiles, nunits, M, breakdown, s);
+    cudaGraph_t g2 = nullptr;
+    cudaError_t e = cudaStreamEndCapture(s, &g2);
+    graph = g2;
+    if (rc) {
+      if (graph) cudaGraphDestroy(graph);
+      return rc;
+    }
+    if (e != cudaSuccess) return rsb_set_cuda_error(e, "cudaStreamEndCapture");
+    e = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return rsb_set_cuda_error(e, "cudaGraphInstantiate");
+  }
+  for (int cyc = 0; cyc < 100000; ++cyc) {
+    if (exec) {
+      cudaError_t e = cudaGraphLaunch(exec, s);
+      rsb_count_launch(3 * M + 3);
+      if (e != cudaSuccess) {
+        cudaGraphExecDestroy(exec);
+        return rsb_set_cuda_error(e, "cudaGraphLaunch");
+      }
+    } else {
+      rc = lz_cycle<V>(a, ntiles, nunits, M, breakdown, s);
+      if (rc) return rc;
+    }
+    rc = read_active(B, s, &active);
+    if (rc || active == 0) break;
+  }
+  if (exec) cudaGraphExecDestroy(exec);
+  return rc;
+}
+
+int solver_lanczos(const LevelGraph& G, const Tile* tiles, int ntiles, Unit* units, int nunits,
+                   const uint64_t* ckey, SolveBufs& B, int f32, int M, uint64_t sd,
+                   const double* from64, const float* from32, int use_graph, cudaStream_t s) {
+  if (ntiles <= 0 || nunits <= 0) return RSB_OK;
+  if (f32)
+    return lanczos_run<float>(G, tiles, ntiles, units, nunits, ckey, B, M, sd, from64, from32,
+                              use_graph, s);
+  return lanczos_run<double>(G, tiles, ntiles, units, nunits, ckey, B, M, sd, from64, from32,
+                             use_graph, s);
+}
+
+// ----------------------------------------------------------------------------
+// inverse iteration with CG
+// ----------------------------------------------------------------------------
+// CG init from w0 / beta0: x = 0, r = p = b, rr = ||b||^2.
+template <typename V>
+__global__ void __launch_bounds__(RSB_BLOCK) k_cg_init(LzArgs<V> a) {
+  __shared__ double sm[RSB_WARPS];
+  __shared__ double out[1];
+  const Tile t = a.tiles[blockIdx.x];
+  Unit& u = a.units[t.unit];
+  if (u.status != U_ACTIVE) return;
+  const V s = V(1.0 / u.beta0);
+  Acc<V> acc;
+  for (int r = t.row0 + threadIdx.x; r < t.row1; r += RSB_BLOCK) {
+    const V b = s * a.W0[r];
+    a.X[r] = V(0);
+    a.R[r] = b;
+    a.P[r] = b;
+    acc.add(b * b);
+  }
+  const double sum = block_sum(acc.get(), sm);
+  if (threadIdx.x == 0) a.partials[blockIdx.x] = sum;
+  if (last_cta(&u.cnt, u.ntile)) {
+    final_reduce(a.partials, a.stride, u.tile0, u.ntile, 1, out);
+    if (threadIdx.x == 0) {
+      u.rr = out[0];
+      u.bnorm = sqrt(out[0]);
+      u.inner = 0;
+      u.cg_done = 0;
+    }
+  }
+}
+
+// AP = L P, pAp -> alpha
+template <typename V>
+__global__ void __launch_bounds__(RSB_BLOCK) k_cg_ap(LzArgs<V> a) {
+  __shared__ double sm[RSB_WARPS];
+  __shared__ double out[1];
+  const Tile t = a.tiles[blockIdx.x];
+  Unit& u = a.units[t.unit];
+  if (u.status != U_ACTIVE || u.cg_done) return;
+  Acc<V> acc;
+  for (int r = t.row0 + threadIdx.x; r < t.row1; r += RSB_BLOCK) {
+    const V pr = a.P[r];
+    const V ap = spmv_row<V>(a.slice_ptr, a.ent, a.P, r, pr);
+    a.AP[r] = ap;
+    acc.add(pr * ap);
+  }
+  const double sum = block_sum(acc.get(), sm);
+  if (threadIdx.x == 0) a.partials[blockIdx.x] = sum;
+  if (last_cta(&u.cnt, u.ntile)) {
+    final_reduce(a.partials, a.stride, u.tile0, u.ntile, 1, out);
+    if (threadIdx.x == 0) u.cg_alpha = u.rr / out[0];
+  }
+}
+
+// x += alpha p, r -= alpha Ap; sums for ||r||^2 and the projection of r.
+template <typename V>
+__global__ void __launch_bounds__(RSB_BLOCK) k_cg_xr(LzArgs<V> a, double cg_tol, int cg_maxit,
+                                                     int* n_cg) {
+  __shared__ double sm[RSB_WARPS];
+  __shared__ double out[2 + RSB_MAXD];
+  const Tile t = a.tiles[blockIdx.x];
+  Unit& u = a.units[t.unit];
+  if (u.status != U_ACTIVE || u.cg_done) return;
+  const int nd = u.nd;
+  const V al = V(u.cg_alpha);
+  Acc<V> r2, rs, d0, d1;
+  for (int r = t.row0 + threadIdx.x; r < t.row1; r += RSB_BLOCK) {
+    a.X[r] += al * a.P[r];
+    const V rr = a.R[r] - al * a.AP[r];
+    a.R[r] = rr;
+    r2.add(rr * rr);
+    rs.add(rr);
+    if (nd > 0) d0.add(V(a.D0[r]) * rr);
+    if (nd > 1) d1.add(V(a.D1[r]) * rr);
+  }
+  double v[4] = {r2.get(), rs.get(), d0.get(), d1.get()};
+  const int nv = 2 + nd;
+  for (int c = 0; c < nv; ++c) {
+    const double sum = block_sum(v[c], sm);
+    if (threadIdx.x == 0) a.partials[(long long)c * a.stride + blockIdx.x] = sum;
+  }
+  if (last_cta(&u.cnt, u.ntile)) {
+    final_reduce(a.partials, a.stride, u.tile0, u.ntile, nv, out);
+    if (threadIdx.x == 0) {
+      double cp2 = 0.0;
+      u.cp[0] = out[1] * u.isn;
+      cp2 += u.cp[0] * u.cp[0];
+      for (int l = 0; l < nd; ++l) {
+        u.cp[1 + l] = out[2 + l];
+        cp2 += u.cp[1 + l] * u.cp[1 + l];
+      }
+      const double rrn = fmax(out[0] - cp2, 0.0);
+      u.inner += 1;
+      u.inner_total += 1;
+      if (sqrt(rrn) <= cg_tol * u.bnorm || u.inner >= cg_maxit) {
+        u.cg_done = 1;
+        atomicSub(n_cg, 1);
+      } else {
+        u.cg_beta = rrn / u.rr;
+        u.rr = rrn;
+      }
+    }
+  }
+}
+
+// r -= B cp (projection), p = r + beta p while CG continues.
+template <typename V>
+__global__ void __launch_bounds__(RSB_BLOCK) k_cg_p(LzArgs<V> a) {
+  const Tile t = a.tiles[blockIdx.x];
+  const Unit& u = a.units[t.unit];
+  if (u.status != U_ACTIVE || u.cg_done) return;
+  const int nd = u.nd;
+  const V be = V(u.cg_beta);
+  for (int r = t.row0 + threadIdx.x; r < t.row1; r += RSB_BLOCK) {
+    V v = a.R[r];
+    if (unit_has(u, a.ckey, r)) v -= V(u.cp[0] * u.isn);
+    if (nd > 0) v -= V(u.cp[1]) * V(a.D0[r]);
+    if (nd > 1) v -= V(u.cp[2]) * V(a.D1[r]);
+    a.R[r] = v;
+    a.P[r] = v + be * a.P[r];
+  }
+}
+
+// Outer step: y = x; Ly, yLy, yy -> Rayleigh quotient.
+template <typename V>
+__global__ void __launch_bounds__(RSB_BLOCK) k_inv_rq(LzArgs<V> a) {
+  __shared__ double sm[RSB_WARPS];
+  __shared__ double out[2];
+  const Tile t = a.tiles[blockIdx.x];
+  Unit& u = a.units[t.unit];
+  if (u.status != U_ACTIVE) return;
+  Acc<V> yly, yy;
+  for (int r = t.row0 + threadIdx.x; r < t.row1; r += RSB_BLOCK) {
+    const V yr = a.X[r];
+    const V ly = spmv_row<V>(a.slice_ptr, a.ent, a.X, r, yr);
+    a.AP[r] = ly;
+    yly.add(yr * ly);
+    yy.add(yr * yr);
+  }
+  double v[2] = {yly.get(), yy.get()};
+  for (int c = 0; c < 2; ++c) {
+    const double sum = block_sum(v[c], sm);
+    if (threadIdx.x == 0) a.partials[(long long)c * a.stride + blockIdx.x] = sum;
+  }
+  if (last_cta(&u.cnt, u.ntile)) {
+    final_reduce(a.partials, a.stride, u.tile0, u.ntile, 2, out);
+    if (threadIdx.x == 0) {
+      u.theta = out[0] / out[1];
+      u.ynorm2 = out[1];
+    }
+  }
+}
+
+// Outer step: residual ||Ly - lambda y|| / ||y||, stop tests, projection dots
+// of y for the next right-hand side.
+template <typename V>
+__global__ void __launch_bounds__(RSB_BLOCK) k_inv_res(LzArgs<V> a, int max_outer) {
+  __shared__ double sm[RSB_WARPS];
+  __shared__ double out[2 + RSB_MAXD];
+  const Tile t = a.tiles[blockIdx.x];
+  Unit& u = a.units[t.unit];
+  if (u.status != U_ACTIVE) return;
+  const int nd = u.nd;
+  const V th = V(u.theta);
+  Acc<V> r2, ys, d0, d1;
+  for (int r = t.row0 + threadIdx.x; r < t.row1; r += RSB_BLOCK) {
+    const V yr = a.X[r];
+    const V res = a.AP[r] - th * yr;
+    r2.add(res * res);
+    ys.add(yr);
+    if (nd > 0) d0.add(V(a.D0[r]) * yr);
+    if (nd > 1) d1.add(V(a.D1[r]) * yr);
+  }
+  double v[4] = {r2.get(), ys.get(), d0.get(), d1.get()};
+  const int nv = 2 + nd;
+  for (int c = 0; c < nv; ++c) {
+    const double sum = block_sum(v[c], sm);
+    if (threadIdx.x == 0) a.partials[(long long)c * a.stride + blockIdx.x] = sum;
+  }
+  if (last_cta(&u.cnt, u.ntile)) {
+    final_reduce(a.partials, a.stride, u.tile0, u.ntile, nv, out);
+    if (threadIdx.x == 0) {
+      u.resid = sqrt(out[0] / u.ynorm2);
+      u.cp[0] = out[1] * u.isn;
+      for (int l = 0; l < nd; ++l) u.cp[1 + l] = out[2 + l];
+      u.cycles += 1;
+      atomicAdd((unsigned long long*)a.stat_cycles, 1ull);
+      int st = U_ACTIVE;
+      if (u.resid <= u.tolabs || u.inner == 1) st = U_CONVERGED;
+      else if (u.cycles >= max_outer) st = U_CAPPED;
+      if (st != U_ACTIVE) {
+        u.status = st;
+        atomicSub(a.n_active, 1);
+      }
+    }
+  }
+}
+
+__global__ void k_count_cg(Unit* units, int nunits, int* n_cg) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < nunits && units[i].status == U_ACTIVE && !units[i].cg_done) atomicAdd(n_cg, 1);
+}
+
+template <typename V>
+static int cg_block(LzArgs<V>& a, int ntiles, int iters, double cg_tol, int cg_maxit, int* n_cg,
+                    cudaStream_t s) {
+  for (int i = 0; i < iters; ++i) {
+    k_cg_ap<V><<<ntiles, RSB_BLOCK, 0, s>>>(a);
+    RSB_CKL("k_cg_ap");
+    k_cg_xr<V><<<ntiles, RSB_BLOCK, 0, s>>>(a, cg_tol, cg_maxit, n_cg);
+    RSB_CKL("k_cg_xr");
+    k_cg_p<V><<<ntiles, RSB_BLOCK, 0, s>>>(a);
+    RSB_CKL("k_cg_p");
+  }
+  return RSB_OK;
+}
+
+template <typename V>
+static int inverse_run(const LevelGraph& G, const Tile* tiles, int ntiles, Unit* units, int nunits,
+                       const uint64_t* ckey, SolveBufs& B, uint64_t sd, const double* from64,
+                       const float* from32, double cg_tol, int cg_maxit, int max_outer,
+                       int use_graph, int64_t* inner_out, cudaStream_t s) {
+  LzArgs<V> a = make_args<V>(G, tiles, ntiles, units, ckey, B);
+  int active = 0;
+  int rc = read_active(B, s, &active);
+  if (rc || active == 0) return rc;
+  rc = lz_start<V>(a, ntiles, sd, from64, from32, s);  // W0 = projected start, beta0
+  if (rc) return rc;
+  const int CGK = 8;
+  cudaGraphExec_t exec = nullptr;
+  if (use_graph) {
+    cudaGraph_t graph = nullptr;
+    RSB_CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+    rc = cg_block<V>(a, ntiles, CGK, cg_tol, cg_maxit, B.n_cg, s);
+    cudaError_t e = cudaStreamEndCapture(s, &graph);
+    if (rc) {
+      if (graph) cudaGraphDestroy(graph);
+      return rc;
+    }
+    if (e != cudaSuccess) return rsb_set_cuda_error(e, "cudaStreamEndCapture");
+    e = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return rsb_set_cuda_error(e, "cudaGraphInstantiate");
+  }
+  for (int outer = 0; outer < max_outer + 1 && active > 0; ++outer) {
+    k_cg_init<V><<<ntiles, RSB_BLOCK, 0, s>>>(a);
+    RSB_CKL("k_cg_init");
+    RSB_CK(cudaMemsetAsync(B.n_cg, 0, sizeof(int), s));
+    k_count_cg<<<(nunits + 127) / 128, 128, 0, s>>>(units, nunits, B.n_cg);
+    RSB_CKL("k_count_cg");
+    for (int blk = 0; blk < cg_maxit / CGK + 2; ++blk) {
+      if (exec) {
+        cudaError_t e = cudaGraphLaunch(exec, s);
+        rsb_count_launch(3 * CGK);
+        if (e != cudaSuccess) {
+          cudaGraphExecDestroy(exec);
+          return rsb_set_cuda_error(e, "cudaGraphLaunch");
+        }
+      } else {
+        rc = cg_block<V>(a, ntiles, CGK, cg_tol, cg_maxit, B.n_cg, s);
+        if (rc) break;
+      }
+      int ncg = 0;
+      RSB_CK(cudaMemcpyAsync(B.h_active, B.n_cg, sizeof(int), cudaMemcpyDeviceToHost, s));
+      RSB_CK(cudaStreamSynchronize(s));
+      ncg = *B.h_active;
+      if (ncg <= 0) break;
+    }
+    if (rc) break;
+    k_inv_rq<V><<<ntiles, RSB_BLOCK, 0, s>>>(a);
+    RSB_CKL("k_inv_rq");
+    k_inv_res<V><<<ntiles, RSB_BLOCK, 0, s>>>(a, max_outer);
+    RSB_CKL("k_inv_res");
+    rc = read_active(B, s, &active);
+    if (rc || active == 0) break;
+    // next right-hand side: x projected (second pass) and normalised into W0
+    k_proj2<V><<<ntiles, RSB_BLOCK, 0, s>>>(a, a.X);
+    RSB_CKL("k_proj2");
+    k_proj3<V><<<ntiles, RSB_BLOCK, 0, s>>>(a, a.X);
+    RSB_CKL("k_proj3");
+  }
+  if (exec) cudaGraphExecDestroy(exec);
+  (void)inner_out;
+  return rc;
+}
+
+int solver_inverse(const LevelGraph& G, const Tile* tiles, int ntiles, Unit* units, int nunits,
+                   const uint64_t* ckey, SolveBufs& B, int f32, uint64_t sd, const double* from64,
+                   const float* from32, double cg_tol, int cg_maxit, int max_outer, int use_graph,
+                   cudaStream_t s) {
+  if (ntiles <= 0 || nunits <= 0) return RSB_OK;
+  if (f32)
+    return inverse_run<float>(G, tiles, ntiles, units, nunits, ckey, B, sd, from64, from32, cg_tol,
+                              cg_maxit, max_outer, use_graph, nullptr, s);
+  return inverse_run<double>(G, tiles, ntiles, units, nunits, ckey, B, sd, from64, from32, cg_tol,
+                             cg_maxit, max_outer, use_graph, nullptr, s);
+}
+
+// ----------------------------------------------------------------------------
+// result vector: out = y / ||y|| (FP64), for units that took part in the solve
+// ----------------------------------------------------------------------------
+template <typename V>
+__global__ void __launch_bounds__(RSB_BLOCK) k_write_vec(LzArgs<V> a, const V* __restrict__ y,
+                                                         double* out, int cand) {
+  const Tile t = a.tiles[blockIdx.x];
+  Unit& u = a.units[t.unit];
+  if (u.status != U_CONVERGED && u.status != U_CAPPED) return;
+  const double sc = 1.0 / sqrt(u.ynorm2);
+  for (int r = t.row0 + threadIdx.x; r < t.row1; r += RSB_BLOCK) out[r] = sc * (double)y[r];
+  if (blockIdx.x == u.tile0 && threadIdx.x == 0 && cand >= 0) {
+    u.lam[cand] = u.theta;
+    u.res[cand] = u.resid;
+  }
+}
+
+int solver_write_vector(const LevelGraph& G, const Tile* tiles, int ntiles, Unit* units,
+                        const uint64_t* ckey, SolveBufs& B, int f32, int from_x, double* out,
+                        int cand, cudaStream_t s) {
+  if (ntiles <= 0) return RSB_OK;
+  if (f32) {
+    LzArgs<float> a = make_args<float>(G, tiles, ntiles, units, ckey, B);
+    k_write_vec<float><<<ntiles, RSB_BLOCK, 0, s>>>(a, from_x ? a.X : a.Y, out, cand);
+  } else {
+    LzArgs<double> a = make_args<double>(G, tiles, ntiles, units, ckey, B);
+    k_write_vec<double><<<ntiles, RSB_BLOCK, 0, s>>>(a, from_x ? a.X : a.Y, out, cand);
+  }
+  RSB_CKL("k_write_vec");
+  return RSB_OK;
+}
+
+// ----------------------------------------------------------------------------
+// R5: rotation of a 2- or 3-dimensional cluster basis minimising sum (U R)^4
+// ----------------------------------------------------------------------------
+// Moments M[a][b][c][d] = sum_r U_a U_b U_c U_d over unit rows, stored for
+// a <= b <= c <= d (15 for three columns); the rotation is then found from the
+// tensor alone by cyclic pairwise steps, each the closed-form optimum of a
+// 2-D rotation (maximise sum (x' y')^2).
+__device__ __forceinline__ int mom_index(int a, int b, int c, int d) {
+  // sort a<=b<=c<=d then enumerate combinations with repetition of {0,1,2}
+  int v[4] = {a, b, c, d};
+  for (int i = 0; i < 4; ++i)
+    for (int j = i + 1; j < 4; ++j)
+      if (v[j] < v[i]) { const int t = v[i]; v[i] = v[j]; v[j] = t; }
+  int idx = 0;
+  for (int p = 0; p < 3; ++p)
+    for (int q = p; q < 3; ++q)
+      for (int r = q; r < 3; ++r)
+        for (int s = r; s < 3; ++s) {
+          if (p == v[0] && q == v[1] && r == v[2] && s == v[3]) return idx;
+          ++idx;
+        }
+  return 0;
+}
+
+__global__ void __launch_bounds__(RSB_BLOCK)
+    k_quartic_moments(const Tile* __restrict__ tiles, Unit* units, const uint64_t* __restrict__ ckey,
+                      const double* __restrict__ v0, const double* __restrict__ v1,
+                      const double* __restrict__ v2, double* partials, long long stride,
+                      double* mom) {
+  __shared__ double sm[RSB_WARPS];
+  __shared__ double out[15];
+  const Tile t = tiles[blockIdx.x];
+  Unit& u = units[t.unit];
+  if (!u.valid || u.ncand < 2) return;
+  const int m = u.ncand;
+  double acc[15];
+  for (int i = 0; i < 15; ++i) acc[i] = 0.0;
+  for (int r = t.row0 + threadIdx.x; r < t.row1; r += RSB_BLOCK) {
+    if (!unit_has(u, ckey, r)) continue;
+    const double x[3] = {v0[r], v1[r], m > 2 ? v2[r] : 0.0};
+    int idx = 0;
+    for (int p = 0; p < 3; ++p)
+      for (int q = p; q < 3; ++q)
+        for (int rr = q; rr < 3; ++rr)
+          for (int s = rr; s < 3; ++s) acc[idx++] += x[p] * x[q] * x[rr] * x[s];
+  }
+  for (int c = 0; c < 15; ++c) {
+    const double sum = block_sum(acc[c], sm);
+    if (threadIdx.x == 0) partials[(long long)c * stride + blockIdx.x] = sum;
+  }
+  if (last_cta(&u.cnt, u.ntile)) {
+    final_reduce(partials, stride, u.tile0, u.ntile, 15, out);
+    if (threadIdx.x < 15) mom[(long long)t.unit * 24 + threadIdx.x] = out[threadIdx.x];
+  }
+}
+
+// S(p,q; i) = sum_r x^(4-i) y^i with x = U R[:,p], y = U R[:,q], from the full
+// (81-entry) moment tensor Mf.
+__device__ double rot_moment(const double* Mf, const double* R, int p, int q, int i) {
+  double s = 0.0;
+  for (int a = 0; a < 3; ++a) {
+    const double fa = R[a * 3 + (0 < 4 - i ? p : q)];
+    for (int b = 0; b < 3; ++b) {
+      const double fab = fa * R[b * 3 + (1 < 4 - i ? p : q)];
+      for (int c = 0; c < 3; ++c) {
+        const double fabc = fab * R[c * 3 + (2 < 4 - i ? p : q)];
+        const double* row = Mf + ((a * 3 + b) * 3 + c) * 3;
+        const int col = 3 < 4 - i ? p : q;
+        s += fabc * (row[0] * R[0 * 3 + col] + row[1] * R[1 * 3 + col] + row[2] * R[2 * 3 + col]);
+      }
+    }
+  }
+  return s;
+}
+
+__global__ void k_quartic_rotation(Unit* units, int nunits, double* mom) {
+  const int ui = blockIdx.x * blockDim.x + threadIdx.x;
+  if (ui >= nunits) return;
+  Unit& u = units[ui];
+  if (!u.valid || u.ncand < 2) return;
+  const int m = u.ncand;
+  double* M = mom + (long long)ui * 24;
+  double Mf[81];
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b)
+      for (int c = 0; c < 3; ++c)
+        for (int d = 0; d < 3; ++d) Mf[((a * 3 + b) * 3 + c) * 3 + d] = M[mom_index(a, b, c, d)];
+  double R[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1};
+  const int sweeps = m > 2 ? 50 : 1;
+  for (int sw = 0; sw < sweeps; ++sw) {
+    double dmax = 0.0;
+    for (int p = 0; p < m - 1; ++p)
+      for (int q = p + 1; q < m; ++q) {
+        const double x4 = rot_moment(Mf, R, p, q, 0);
+        const double x3y = rot_moment(Mf, R, p, q, 1);
+        const double x2y2 = rot_moment(Mf, R, p, q, 2);
+        const double xy3 = rot_moment(Mf, R, p, q, 3);
+        const double y4 = rot_moment(Mf, R, p, q, 4);
+        // u = x^2 - y^2, w = 2 x y
+        const double uu = x4 - 2.0 * x2y2 + y4;
+        const double ww = 4.0 * x2y2;
+        const double uw = 2.0 * (x3y - xy3);
+        const double th = 0.25 * atan2(uw, 0.5 * (ww - uu));
+        const double c = cos(th), s = sin(th);
+        for (int a = 0; a < 3; ++a) {
+          const double rp = R[a * 3 + p], rq = R[a * 3 + q];
+          R[a * 3 + p] = c * rp - s * rq;
+          R[a * 3 + q] = s * rp + c * rq;
+        }
+        dmax = fmax(dmax, fabs(th));
+      }
+    if (dmax < 1e-12) break;
+  }
+  for (int i = 0; i < 9; ++i) M[15 + i] = R[i];
+}
+
+__global__ void __launch_bounds__(RSB_BLOCK)
+    k_quartic_apply(const Tile* __restrict__ tiles, const Unit* units, double* v0, double* v1,
+                    double* v2, const double* mom) {
+  const Tile t = tiles[blockIdx.x];
+  const Unit& u = units[t.unit];
+  if (!u.valid || u.ncand < 2) return;
+  const int m = u.ncand;
+  const double* R = mom + (long long)t.unit * 24 + 15;
+  for (int r = t.row0 + threadIdx.x; r < t.row1; r += RSB_BLOCK) {
+    const double x[3] = {v0[r], v1[r], m > 2 ? v2[r] : 0.0};
+    double y[3];
+    for (int c = 0; c < m; ++c) {
+      double s = 0.0;
+      for (int a = 0; a < m; ++a) s += x[a] * R[a * 3 + c];
+      y[c] = s;
+    }
+    v0[r] = y[0];
+    v1[r] = y[1];
+    if (m > 2) v2[r] = y[2];
+  }
+}
+
+int solver_quartic(const Tile* tiles, int ntiles, Unit* units, int nunits, const uint64_t* ckey,
+                   double* v0, double* v1, double* v2, double* partials, double* mom,
+                   cudaStream_t s) {
+  if (ntiles <= 0) return RSB_OK;
+  k_quartic_moments<<<ntiles, RSB_BLOCK, 0, s>>>(tiles, units, ckey, v0, v1, v2, partials, ntiles,
+                                                 mom);
+  RSB_CKL("k_quartic_moments");
+  k_quartic_rotation<<<(nunits + 63) / 64, 64, 0, s>>>(units, nunits, mom);
+  RSB_CKL("k_quartic_rotation");
+  k_quartic_apply<<<ntiles, RSB_BLOCK, 0, s>>>(tiles, units, v0, v1, v2, mom);
+  RSB_CKL("k_quartic_apply");
+  return RSB_OK;
+}
+
+// ----------------------------------------------------------------------------
+// cluster test after a deflated solve (R5): candidate nd joins when its
+// eigenvalue is within cluster_tol * lambda_a of the first.
+// ----------------------------------------------------------------------------
+__global__ void k_cluster_check(Unit* units, int nunits, int nd, double cluster_tol) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nunits) return;
+  Unit& u = units[i];
+  if (!u.valid || u.ncand != nd) return;
+  if (u.status != U_CONVERGED && u.status != U_CAPPED) return;
+  if (fabs(u.lam[nd] - u.lam[0]) <= cluster_tol * u.lam[0]) u.ncand = nd + 1;
+}
+
+int solver_cluster_check(Unit* units, int nunits, int nd, double cluster_tol, cudaStream_t s) {
+  k_cluster_check<<<(nunits + 127) / 128, 128, 0, s>>>(units, nunits, nd, cluster_tol);
+  RSB_CKL("k_cluster_check");
+  return RSB_OK;
+}
+
+// Statistics of the finished solve: count capped units, max residual / dmax.
+__global__ void k_solve_stats(const Unit* units, int nunits, int* capped, double* resid_max,
+                              int cand) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nunits) return;
+  const Unit& u = units[i];
+  if (u.status == U_CAPPED) atomicAdd(capped, 1);
+  if (u.status == U_CONVERGED || u.status == U_CAPPED) {
+    const double r = u.resid / fmax(u.dmax, 1e-300);
+    // non-negative doubles order like their bit patterns
+    atomicMax((unsigned long long*)resid_max, (unsigned long long)__double_as_longlong(r));
+  }
+  (void)cand;
+}
+
+int solver_stats(const Unit* units, int nunits, int* capped, double* resid_max, cudaStream_t s) {
+  k_solve_stats<<<(nunits + 127) / 128, 128, 0, s>>>(units, nunits, capped, resid_max, 0);
+  RSB_CKL("k_solve_stats");
+  return RSB_OK;
+}
