@@ -91,6 +91,8 @@ typedef struct rsb_options {
   int batched;           /* 1: all subgraphs of a level in one set of launches     */
   int use_graph;         /* 1: capture each Lanczos cycle / CG block in a CUDA graph */
   int validate;          /* 1: also check symmetry of the input on the device      */
+  int polish_cycles;     /* MIXED: FP64 Lanczos cycles after the FP32 stage (0: only
+                            the FP64 Rayleigh-quotient refinement of the FP32 vector) */
 } rsb_options;
 
 typedef struct rsb_stats {
@@ -108,8 +110,23 @@ typedef struct rsb_stats {
 
 /* Fills *o with the defaults: Lanczos, FP64, krylov_dim 40, max_restarts 50,
  * tol 1e-10, cg_tol 1e-12, cg_maxit 4000, max_outer 50, RESOLVE,
- * cluster_tol 0.05, tie_rel 1e-5, mixed_tol 1e-6, batched 1, use_graph 1. */
+ * cluster_tol 0.05, tie_rel 1e-5, mixed_tol 1e-6, batched 1, use_graph 1,
+ * validate 0, polish_cycles 0. */
 void rsb_options_default(rsb_options *o);
+
+/*
+ * Kernel timing for bandwidth accounting (not part of the method).
+ * rsb_profile_begin(family) makes the following calls bracket every launch of
+ * one kernel family with CUDA events on the library's stream and add up the
+ * algorithmic bytes of each launch; rsb_profile_end() returns the totals and
+ * switches timing off.  family: 1 Lanczos step A (SpMV + first Gram-Schmidt
+ * dots), 2 step B (update + second dots), 3 step C (update + norm), 4 CG
+ * Laplacian action, 5 Laplacian action of rsb_laplacian_bench.
+ * Bytes count 4 B per stored SELL entry (padding included), every vector
+ * element read or written once, and FP64 deflation vectors.
+ */
+void rsb_profile_begin(int family);
+void rsb_profile_end(double *ms_total, int64_t *launches, double *bytes_total);
 
 /*
  * Recursive spectral bisection of one graph into nparts parts (§4,

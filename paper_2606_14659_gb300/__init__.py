@@ -6,5 +6,6 @@ The compute path is the CUDA library librsb.so (csrc/, C ABI in include/rsb.h);
 from . import rsb  # noqa: F401
 from .rsb import (  # noqa: F401
     Graph, graph, options, rsb_partition, rsb_partition_batch, rsb_fiedler,
-    rsb_laplacian_apply, rsb_laplacian_bench, rsb_release, RSBError,
+    rsb_laplacian_apply, rsb_laplacian_bench, rsb_release, RSBError, rsb_profile_begin,
+    rsb_profile_end,
 )

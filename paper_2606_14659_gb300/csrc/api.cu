@@ -63,6 +63,8 @@ int solver_quartic(const Tile* tiles, int ntiles, Unit* units, int nunits, const
                    cudaStream_t s);
 int solver_cluster_check(Unit* units, int nunits, int nd, double cluster_tol, cudaStream_t s);
 int solver_stats(const Unit* units, int nunits, int* capped, double* resid_max, cudaStream_t s);
+int solver_rq_refine(const LevelGraph& G, const Tile* tiles, int ntiles, Unit* units, int nunits,
+                     const uint64_t* ckey, SolveBufs& B, const float* from32, cudaStream_t s);
 
 // ----------------------------------------------------------------------------
 // errors
@@ -79,6 +81,99 @@ int rsb_set_error(int code, const std::string& what) {
   return code;
 }
 void rsb_count_launch(int k) { g_launches += k; }
+
+// ----------------------------------------------------------------------------
+// kernel timing (rsb_profile_begin / rsb_profile_end)
+// ----------------------------------------------------------------------------
+static struct {
+  int family = PROF_NONE;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pool;
+  std::vector<int> free_list, pending;
+  bool capturing = false;
+  std::vector<int> captured;
+  double ms = 0.0;
+  long long launches = 0;
+  unsigned long long* dbytes = nullptr;  // one counter per family
+} g_prof;
+
+int prof_before(int family, cudaStream_t s) {
+  if (g_prof.family == PROF_NONE || family != g_prof.family) return -1;
+  int idx;
+  if (!g_prof.free_list.empty()) {
+    idx = g_prof.free_list.back();
+    g_prof.free_list.pop_back();
+  } else {
+    cudaEvent_t a, b;
+    if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) return -1;
+    g_prof.pool.emplace_back(a, b);
+    idx = (int)g_prof.pool.size() - 1;
+  }
+  cudaEventRecordWithFlags(g_prof.pool[idx].first, s,
+                           g_prof.capturing ? cudaEventRecordExternal : cudaEventRecordDefault);
+  return idx;
+}
+void prof_after(int idx, cudaStream_t s) {
+  if (idx < 0) return;
+  cudaEventRecordWithFlags(g_prof.pool[idx].second, s,
+                           g_prof.capturing ? cudaEventRecordExternal : cudaEventRecordDefault);
+  if (g_prof.capturing) g_prof.captured.push_back(idx);
+  else g_prof.pending.push_back(idx);
+}
+void prof_collect() {
+  for (int idx : g_prof.pending) {
+    float t = 0.f;
+    if (cudaEventElapsedTime(&t, g_prof.pool[idx].first, g_prof.pool[idx].second) == cudaSuccess) {
+      g_prof.ms += t;
+      g_prof.launches += 1;
+    } else {
+      cudaGetLastError();
+    }
+  }
+  g_prof.pending.clear();
+}
+void prof_capture_begin() {
+  g_prof.capturing = true;
+  g_prof.captured.clear();
+}
+std::vector<int> prof_capture_end() {
+  g_prof.capturing = false;
+  std::vector<int> v;
+  v.swap(g_prof.captured);
+  return v;
+}
+void prof_replay(const std::vector<int>& pairs) {
+  g_prof.pending.insert(g_prof.pending.end(), pairs.begin(), pairs.end());
+}
+unsigned long long* prof_bytes(int family) {
+  if (g_prof.family == PROF_NONE || family != g_prof.family || !g_prof.dbytes) return nullptr;
+  return g_prof.dbytes;
+}
+
+extern "C" void rsb_profile_begin(int family) {
+  g_prof.family = (family >= PROF_LZ_A && family <= PROF_SPMV) ? family : PROF_NONE;
+  g_prof.ms = 0.0;
+  g_prof.launches = 0;
+  g_prof.pending.clear();
+  // pairs held by graphs that were destroyed are free again
+  g_prof.free_list.clear();
+  for (int i = 0; i < (int)g_prof.pool.size(); ++i) g_prof.free_list.push_back(i);
+  if (!g_prof.dbytes && cudaMalloc(&g_prof.dbytes, sizeof(unsigned long long)) != cudaSuccess) {
+    cudaGetLastError();
+    g_prof.dbytes = nullptr;
+  }
+  if (g_prof.dbytes) cudaMemset(g_prof.dbytes, 0, sizeof(unsigned long long));
+}
+
+extern "C" void rsb_profile_end(double* ms_total, int64_t* launches, double* bytes_total) {
+  cudaDeviceSynchronize();
+  prof_collect();
+  unsigned long long b = 0;
+  if (g_prof.dbytes) cudaMemcpy(&b, g_prof.dbytes, sizeof(b), cudaMemcpyDeviceToHost);
+  if (ms_total) *ms_total = g_prof.ms;
+  if (launches) *launches = g_prof.launches;
+  if (bytes_total) *bytes_total = (double)b;
+  g_prof.family = PROF_NONE;
+}
 
 int devbuf_reserve(DevBuf& b, size_t bytes) {
   if (bytes <= b.cap) return RSB_OK;
@@ -213,6 +308,7 @@ extern "C" void rsb_options_default(rsb_options* o) {
   o->batched = 1;
   o->use_graph = 1;
   o->validate = 0;
+  o->polish_cycles = 0;
 }
 
 static int check_options(const rsb_options& o) {
@@ -223,7 +319,8 @@ static int check_options(const rsb_options& o) {
   if (o.max_restarts < 1) return rsb_set_error(RSB_EINVAL, "max_restarts");
   if (!(o.tol > 0) || !(o.cg_tol > 0) || !(o.mixed_tol > 0))
     return rsb_set_error(RSB_EINVAL, "tolerances");
-  if (o.cg_maxit < 1 || o.max_outer < 1) return rsb_set_error(RSB_EINVAL, "iteration caps");
+  if (o.cg_maxit < 1 || o.max_outer < 1 || o.polish_cycles < 0)
+    return rsb_set_error(RSB_EINVAL, "iteration caps");
   if (!(o.cluster_tol >= 0) || !(o.tie_rel >= 0)) return rsb_set_error(RSB_EINVAL, "cluster/tie");
   if (o.degenerate_policy != RSB_DEGEN_NONE && o.degenerate_policy != RSB_DEGEN_RESOLVE)
     return rsb_set_error(RSB_EINVAL, "degenerate_policy");
@@ -318,9 +415,11 @@ static void make_tiles(std::vector<Unit>& units, std::vector<Tile>& tiles) {
   for (size_t i = 0; i < units.size(); ++i) {
     Unit& u = units[i];
     const int64_t nr = u.nrows;
+    // rows per thread of a tile: at least RSB_MINR (memory-level parallelism),
+    // more for large units so that a unit has at most RSB_MAXTILES_PER_UNIT tiles
     int64_t R = (nr + (int64_t)RSB_BLOCK * RSB_MAXTILES_PER_UNIT - 1) /
                 ((int64_t)RSB_BLOCK * RSB_MAXTILES_PER_UNIT);
-    if (R < 1) R = 1;
+    if (R < RSB_MINR) R = RSB_MINR;
     const int64_t tr = R * RSB_BLOCK;
     u.tile0 = (int32_t)tiles.size();
     int nt = 0;
@@ -429,19 +528,32 @@ static int solve_candidate(Ctx& c, const LevelGraph& G, const Tile* tiles, int n
   if (!mixed) {
     if ((rc = solver_write_vector(G, tiles, ntiles, units, ckey, B, 0, inverse, out, cand, c.s)))
       return rc;
-  } else {
-    // stage 2: FP64 Lanczos polish started from the FP32 vector
+  } else if (o.polish_cycles > 0) {
+    // stage 2: a bounded number of FP64 Lanczos cycles started from the FP32 vector
     SolveBufs B64 = B;
     if ((rc = reserve_prec(c, 0, G.n, std::max(M, 1), B64))) return rc;
     B64.D[0] = B.D[0];
     B64.D[1] = B.D[1];
-    if ((rc = solver_setup(units, nunits, nd, o.krylov_dim, o.max_restarts, o.tol, require_cluster,
-                           B64, c.s)))
+    if ((rc = solver_setup(units, nunits, nd, o.krylov_dim, o.polish_cycles, o.tol,
+                           require_cluster, B64, c.s)))
       return rc;
     if ((rc = solver_lanczos(G, tiles, ntiles, units, nunits, ckey, B64, 0, M, sd, nullptr,
                              (const float*)stage1_vec, use_graph, c.s)))
       return rc;
     if ((rc = solver_write_vector(G, tiles, ntiles, units, ckey, B64, 0, 0, out, cand, c.s)))
+      return rc;
+  } else {
+    // stage 2: FP64 Rayleigh-quotient refinement of the FP32 vector
+    SolveBufs B64 = B;
+    if ((rc = reserve_prec(c, 0, G.n, 1, B64))) return rc;
+    B64.D[0] = B.D[0];
+    B64.D[1] = B.D[1];
+    if ((rc = solver_setup(units, nunits, nd, o.krylov_dim, 1, tol1, require_cluster, B64, c.s)))
+      return rc;
+    if ((rc = solver_rq_refine(G, tiles, ntiles, units, nunits, ckey, B64,
+                               (const float*)stage1_vec, c.s)))
+      return rc;
+    if ((rc = solver_write_vector(G, tiles, ntiles, units, ckey, B64, 0, 1, out, cand, c.s)))
       return rc;
   }
   // statistics

@@ -206,34 +206,47 @@ int launch_scan_i64(const int64_t* in, int64_t* out_excl, int64_t n, void* tmp, 
 template <typename V>
 __global__ void __launch_bounds__(RSB_BLOCK) k_spmv(const int64_t* __restrict__ slice_ptr,
                                                     const uint32_t* __restrict__ ent, int32_t n,
-                                                    const V* __restrict__ x, V* __restrict__ y) {
+                                                    const V* __restrict__ x, V* __restrict__ y,
+                                                    unsigned long long* pbytes) {
   const int r = blockIdx.x * RSB_BLOCK + threadIdx.x;
-  if (r >= n) return;
-  const int64_t base = slice_ptr[r >> 5];
-  const int width = (int)((slice_ptr[(r >> 5) + 1] - base) >> 5);
-  const uint32_t* e = ent + base + (r & 31);
-  const V xr = x[r];
-  V acc = V(0);
+  int width = 0;
+  if (r < n) {
+    const int64_t base = slice_ptr[r >> 5];
+    width = (int)((slice_ptr[(r >> 5) + 1] - base) >> 5);
+    const uint32_t* e = ent + base + (r & 31);
+    const V xr = x[r];
+    V acc = V(0);
 #pragma unroll 4
-  for (int k = 0; k < width; ++k) {
-    const uint32_t p = __ldg(e + 32 * k);
-    acc += V(ent_w(p)) * (xr - __ldg(x + ent_col(p)));
+    for (int k = 0; k < width; ++k) {
+      const uint32_t p = __ldg(e + 32 * k);
+      acc += V(ent_w(p)) * (xr - __ldg(x + ent_col(p)));
+    }
+    y[r] = acc;
   }
-  y[r] = acc;
+  if (pbytes) {  // algorithmic bytes: entries, x once, y once
+    unsigned long long b = r < n ? 4ull * width + 2ull * sizeof(V) : 0ull;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) b += __shfl_xor_sync(0xffffffffu, b, o);
+    if ((threadIdx.x & 31) == 0) atomicAdd(pbytes, b);
+  }
 }
 
 int launch_spmv_f64(const LevelGraph& G, const double* x, double* y, cudaStream_t s) {
   if (G.n <= 0) return RSB_OK;
+  const int pi = prof_before(PROF_SPMV, s);
   k_spmv<double><<<(G.n + RSB_BLOCK - 1) / RSB_BLOCK, RSB_BLOCK, 0, s>>>(G.slice_ptr, G.ent, G.n,
-                                                                         x, y);
+                                                                         x, y, prof_bytes(PROF_SPMV));
   RSB_CKL("k_spmv<f64>");
+  prof_after(pi, s);
   return RSB_OK;
 }
 int launch_spmv_f32(const LevelGraph& G, const float* x, float* y, cudaStream_t s) {
   if (G.n <= 0) return RSB_OK;
+  const int pi = prof_before(PROF_SPMV, s);
   k_spmv<float><<<(G.n + RSB_BLOCK - 1) / RSB_BLOCK, RSB_BLOCK, 0, s>>>(G.slice_ptr, G.ent, G.n, x,
-                                                                        y);
+                                                                        y, prof_bytes(PROF_SPMV));
   RSB_CKL("k_spmv<f32>");
+  prof_after(pi, s);
   return RSB_OK;
 }
 

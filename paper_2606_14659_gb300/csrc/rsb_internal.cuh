@@ -36,6 +36,8 @@
 #define RSB_MAXD 2                        // deflation vectors (cluster dim 3)
 #define RSB_MAXC (1 + RSB_MAXD + RSB_MAXM)  // Gram-Schmidt coefficients
 #define RSB_MAXTILES_PER_UNIT 1024
+#define RSB_MINR 2    // minimum rows per thread of a tile
+#define RSB_SUBR 8    // rows per thread handled between two CTA barriers
 #define RSB_COLBITS 29
 #define RSB_COLMASK 0x1FFFFFFFu
 #define RSB_MAXN (1 << RSB_COLBITS)
@@ -217,9 +219,17 @@ __device__ __forceinline__ void final_reduce(const double* partials, long long s
                                              int nt, int nc, double* out) {
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   for (int c = w; c < nc; c += RSB_WARPS) {
-    double s = 0.0;
-    for (int t = lane; t < nt; t += 32) s += __ldcg(partials + (long long)c * stride + t0 + t);
-    s = warp_sum(s);
+    const double* p = partials + (long long)c * stride + t0;
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+    int t = lane;
+    for (; t + 96 < nt; t += 128) {
+      s0 += __ldcg(p + t);
+      s1 += __ldcg(p + t + 32);
+      s2 += __ldcg(p + t + 64);
+      s3 += __ldcg(p + t + 96);
+    }
+    for (; t < nt; t += 32) s0 += __ldcg(p + t);
+    double s = warp_sum((s0 + s1) + (s2 + s3));
     if (lane == 0) out[c] = s;
   }
   __syncthreads();
@@ -258,6 +268,16 @@ struct SegHost {
 int rsb_set_cuda_error(cudaError_t e, const char* where);
 int rsb_set_error(int code, const std::string& what);
 void rsb_count_launch(int k = 1);
+
+// Kernel timing (rsb_profile_begin/end): families of include/rsb.h.
+enum { PROF_NONE = 0, PROF_LZ_A = 1, PROF_LZ_B = 2, PROF_LZ_C = 3, PROF_CG_AP = 4, PROF_SPMV = 5 };
+int prof_before(int family, cudaStream_t s);      // event pair index or -1
+void prof_after(int idx, cudaStream_t s);
+void prof_collect();                              // after a stream sync
+void prof_capture_begin();
+std::vector<int> prof_capture_end();              // pairs recorded during a capture
+void prof_replay(const std::vector<int>& pairs);  // a graph holding them was launched
+unsigned long long* prof_bytes(int family);       // device byte counter or nullptr
 
 #define RSB_CK(call)                                              \
   do {                                                            \

@@ -49,7 +49,22 @@ struct LzArgs {
   long long stride;
   int* n_active;
   long long* stat_cycles;
+  unsigned long long* pb_a;  // profiling byte counters (nullptr when off)
+  unsigned long long* pb_b;
+  unsigned long long* pb_c;
+  unsigned long long* pb_cg;
 };
+
+// CTA-level add of per-thread byte counts to a profiling counter.
+__device__ __forceinline__ void prof_add(unsigned long long* pb, unsigned long long b) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) b += __shfl_xor_sync(0xffffffffu, b, o);
+  if ((threadIdx.x & 31) == 0) atomicAdd(pb, b);
+}
+
+__device__ __forceinline__ int row_width(const int64_t* __restrict__ slice_ptr, int r) {
+  return (int)((slice_ptr[(r >> 5) + 1] - slice_ptr[r >> 5]) >> 5);
+}
 
 template <typename V>
 __device__ __forceinline__ V spmv_row(const int64_t* __restrict__ slice_ptr,
@@ -67,32 +82,54 @@ __device__ __forceinline__ V spmv_row(const int64_t* __restrict__ slice_ptr,
   return acc;
 }
 
-// Basis vector c of the Gram-Schmidt set [u0, D_0.., q_0..] at row r.
-// u0 = 1/sqrt(n) on unit rows; callers multiply by isn themselves where it
-// matters (its dot is taken as a plain sum).
-template <typename V>
-__device__ __forceinline__ V basis_at(const LzArgs<V>& a, int nd, int c, int r) {
-  if (c == 0) return V(1);
-  if (c <= nd) return V((c == 1 ? a.D0 : a.D1)[r]);
-  return a.Q[(long long)(c - 1 - nd) * a.N + r];
+// ----------------------------------------------------------------------------
+// Gram-Schmidt building blocks.  The basis is [u0, D_0.., q_0..q_j] with
+// u0 = 1/sqrt(n) on unit rows (its dot is taken as a plain sum and scaled by
+// 1/sqrt(n) afterwards).  A CTA handles its tile in sub-chunks of up to
+// RSB_BLOCK * RSB_SUBR rows: phase 1 computes the chunk's w (one row per
+// thread and RSB_SUBR rows per thread, coefficient-outer so that every
+// thread has RSB_SUBR independent loads in flight), stores it in shared
+// memory; phase 2 takes the dot products warp-per-coefficient with unrolled
+// coalesced loads.
+// ----------------------------------------------------------------------------
+#define MAXCW ((RSB_MAXC + RSB_WARPS - 1) / RSB_WARPS)
+#define SUBROWS (RSB_BLOCK * RSB_SUBR)
+
+template <typename V, typename B>
+__device__ __forceinline__ void dot_rows(const B* __restrict__ bv, const V* ws, int base, int end,
+                                         Acc<V>& acc) {
+  const int lane = threadIdx.x & 31;
+  int row = base + lane;
+  for (; row + 96 < end; row += 128) {
+    const V b0 = V(bv[row]), b1 = V(bv[row + 32]), b2 = V(bv[row + 64]), b3 = V(bv[row + 96]);
+    const int o = row - base;
+    acc.add(b0 * ws[o]);
+    acc.add(b1 * ws[o + 32]);
+    acc.add(b2 * ws[o + 64]);
+    acc.add(b3 * ws[o + 96]);
+  }
+  for (; row < end; row += 32) acc.add(V(bv[row]) * ws[row - base]);
 }
 
-// Warp-per-coefficient dot products of the basis with the 256 values in ws
-// (rows base..base+255 of the tile); coefficient c lives in warp c % 8.
-#define MAXCW ((RSB_MAXC + RSB_WARPS - 1) / RSB_WARPS)
+template <typename V>
+__device__ __forceinline__ void dot_ones(const V* ws, int base, int end, Acc<V>& acc) {
+  const int lane = threadIdx.x & 31;
+  for (int row = base + lane; row < end; row += 32) acc.add(ws[row - base]);
+}
+
+// Warp-per-coefficient dots of basis coefficients [c0, c0 + nc) with the chunk.
 template <typename V>
 __device__ __forceinline__ void tile_dots(const LzArgs<V>& a, int nd, int c0, int nc, int base,
-                                          int rowend, const V* ws, Acc<V> (&acc)[MAXCW]) {
-  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+                                          int end, const V* ws, Acc<V> (&acc)[MAXCW]) {
+  const int w = threadIdx.x >> 5;
 #pragma unroll
   for (int i = 0; i < MAXCW; ++i) {
     const int c = w + RSB_WARPS * i;
-    if (c >= nc) break;
-    const int cc = c0 + c;
-#pragma unroll 4
-    for (int q = 0; q < 8; ++q) {
-      const int row = base + lane + 32 * q;
-      if (row < rowend) acc[i].add(basis_at(a, nd, cc, row) * ws[lane + 32 * q]);
+    if (c < nc) {
+      const int cc = c0 + c;
+      if (cc == 0) dot_ones<V>(ws, base, end, acc[i]);
+      else if (cc <= nd) dot_rows<V, double>(cc == 1 ? a.D0 : a.D1, ws, base, end, acc[i]);
+      else dot_rows<V, V>(a.Q + (long long)(cc - 1 - nd) * a.N, ws, base, end, acc[i]);
     }
   }
 }
@@ -103,9 +140,46 @@ __device__ __forceinline__ void store_dots(const LzArgs<V>& a, int nc, Acc<V> (&
 #pragma unroll
   for (int i = 0; i < MAXCW; ++i) {
     const int c = w + RSB_WARPS * i;
-    if (c >= nc) break;
-    const double s = warp_sum(acc[i].get());
-    if (lane == 0) a.partials[(long long)c * a.stride + blockIdx.x] = s;
+    if (c < nc) {
+      const double s = warp_sum(acc[i].get());
+      if (lane == 0) a.partials[(long long)c * a.stride + blockIdx.x] = s;
+    }
+  }
+}
+
+// w[rr] -= sum_c coef[c] basis_c for the RSB_SUBR rows of this thread
+// (rows base + rr*RSB_BLOCK + tid), coefficient-outer.
+template <typename V>
+__device__ __forceinline__ void gs_update_rows(const LzArgs<V>& a, const Unit& u,
+                                               const double* coef, int nd, int nq, int base,
+                                               int end, V (&w)[RSB_SUBR]) {
+  const V c0 = V(coef[0] * u.isn);
+#pragma unroll
+  for (int rr = 0; rr < RSB_SUBR; ++rr) {
+    const int r = base + rr * RSB_BLOCK + threadIdx.x;
+    if (r < end && unit_has(u, a.ckey, r)) w[rr] -= c0;
+  }
+  for (int l = 0; l < nd; ++l) {
+    const double* d = l == 0 ? a.D0 : a.D1;
+    const V cl = V(coef[1 + l]);
+#pragma unroll
+    for (int rr = 0; rr < RSB_SUBR; ++rr) {
+      const int r = base + rr * RSB_BLOCK + threadIdx.x;
+      if (r < end) w[rr] -= cl * V(d[r]);
+    }
+  }
+  const double* cq = coef + 1 + nd;
+  for (int k = 0; k < nq; ++k) {
+    const V ck = V(cq[k]);
+    const V* q = a.Q + (long long)k * a.N;
+    V qv[RSB_SUBR];
+#pragma unroll
+    for (int rr = 0; rr < RSB_SUBR; ++rr) {
+      const int r = base + rr * RSB_BLOCK + threadIdx.x;
+      qv[rr] = r < end ? q[r] : V(0);
+    }
+#pragma unroll
+    for (int rr = 0; rr < RSB_SUBR; ++rr) w[rr] -= ck * qv[rr];
   }
 }
 
@@ -114,7 +188,7 @@ __device__ __forceinline__ void store_dots(const LzArgs<V>& a, int nc, Acc<V> (&
 // ----------------------------------------------------------------------------
 template <typename V>
 __global__ void __launch_bounds__(RSB_BLOCK) k_lz_a(LzArgs<V> a, int j) {
-  __shared__ V ws[RSB_BLOCK];
+  __shared__ V ws[SUBROWS];
   __shared__ double out[RSB_MAXC];
   const Tile t = a.tiles[blockIdx.x];
   Unit& u = a.units[t.unit];
@@ -131,22 +205,32 @@ __global__ void __launch_bounds__(RSB_BLOCK) k_lz_a(LzArgs<V> a, int j) {
   const int nc = last ? 1 : (2 + nd + j);
   const int c0 = last ? (1 + nd + j) : 0;
   Acc<V> acc[MAXCW];
-  for (int base = t.row0; base < t.row1; base += RSB_BLOCK) {
-    const int r = base + threadIdx.x;
-    V w = V(0);
-    if (r < t.row1) {
-      const V xr = src[r];
-      w = s * spmv_row<V>(a.slice_ptr, a.ent, src, r, xr);
-      if (j) w -= bj * qjm[r];
-      qj[r] = s * xr;
-      if (!last) dst[r] = w;
+  unsigned long long pbytes = 0;
+  for (int base = t.row0; base < t.row1; base += SUBROWS) {
+    const int end = min(t.row1, base + SUBROWS);
+#pragma unroll 2
+    for (int rr = 0; rr < RSB_SUBR; ++rr) {
+      const int r = base + rr * RSB_BLOCK + threadIdx.x;
+      V w = V(0);
+      if (r < end) {
+        const V xr = src[r];
+        w = s * spmv_row<V>(a.slice_ptr, a.ent, src, r, xr);
+        if (j) w -= bj * qjm[r];
+        qj[r] = s * xr;
+        if (!last) dst[r] = w;
+        if (a.pb_a)
+          pbytes += 4ull * row_width(a.slice_ptr, r) +
+                    sizeof(V) * (unsigned long long)(2 + (j > 0) + !last + (last ? 1 : j + 1)) +
+                    (last ? 0ull : 8ull * nd);
+      }
+      ws[rr * RSB_BLOCK + threadIdx.x] = w;
     }
-    ws[threadIdx.x] = w;
     __syncthreads();
-    tile_dots<V>(a, nd, c0, nc, base, t.row1, ws, acc);
+    tile_dots<V>(a, nd, c0, nc, base, end, ws, acc);
     __syncthreads();
   }
   store_dots<V>(a, nc, acc);
+  if (a.pb_a) prof_add(a.pb_a, pbytes);
   if (last_cta(&u.cnt, u.ntile)) {
     final_reduce(a.partials, a.stride, u.tile0, u.ntile, nc, out);
     if (threadIdx.x == 0) {
@@ -161,23 +245,9 @@ __global__ void __launch_bounds__(RSB_BLOCK) k_lz_a(LzArgs<V> a, int j) {
   }
 }
 
-// w -= sum_c coef[c] basis_c at row r (u0 only on unit rows)
-template <typename V>
-__device__ __forceinline__ V gs_update(const LzArgs<V>& a, const Unit& u, const double* coef,
-                                       int nd, int nq, int r, V w) {
-  if (unit_has(u, a.ckey, r)) w -= V(coef[0] * u.isn);
-  if (nd > 0) w -= V(coef[1]) * V(a.D0[r]);
-  if (nd > 1) w -= V(coef[2]) * V(a.D1[r]);
-  const V* q = a.Q + r;
-  const double* cq = coef + 1 + nd;
-#pragma unroll 4
-  for (int k = 0; k < nq; ++k) w -= V(cq[k]) * q[(long long)k * a.N];
-  return w;
-}
-
 template <typename V>
 __global__ void __launch_bounds__(RSB_BLOCK) k_lz_b(LzArgs<V> a, int j) {
-  __shared__ V ws[RSB_BLOCK];
+  __shared__ V ws[SUBROWS];
   __shared__ double out[RSB_MAXC];
   const Tile t = a.tiles[blockIdx.x];
   Unit& u = a.units[t.unit];
@@ -186,19 +256,31 @@ __global__ void __launch_bounds__(RSB_BLOCK) k_lz_b(LzArgs<V> a, int j) {
   const int nd = u.nd;
   const int nc = 2 + nd + j;
   Acc<V> acc[MAXCW];
-  for (int base = t.row0; base < t.row1; base += RSB_BLOCK) {
-    const int r = base + threadIdx.x;
-    V w = V(0);
-    if (r < t.row1) {
-      w = gs_update<V>(a, u, u.c1, nd, j + 1, r, w_[r]);
-      w_[r] = w;
+  unsigned long long pbytes = 0;
+  for (int base = t.row0; base < t.row1; base += SUBROWS) {
+    const int end = min(t.row1, base + SUBROWS);
+    V w[RSB_SUBR];
+#pragma unroll
+    for (int rr = 0; rr < RSB_SUBR; ++rr) {
+      const int r = base + rr * RSB_BLOCK + threadIdx.x;
+      w[rr] = r < end ? w_[r] : V(0);
     }
-    ws[threadIdx.x] = w;
+    gs_update_rows<V>(a, u, u.c1, nd, j + 1, base, end, w);
+#pragma unroll
+    for (int rr = 0; rr < RSB_SUBR; ++rr) {
+      const int r = base + rr * RSB_BLOCK + threadIdx.x;
+      if (r < end) {
+        w_[r] = w[rr];
+        if (a.pb_b) pbytes += sizeof(V) * (unsigned long long)(3 + j) + 8ull * nd;
+      }
+      ws[rr * RSB_BLOCK + threadIdx.x] = r < end ? w[rr] : V(0);
+    }
     __syncthreads();
-    tile_dots<V>(a, nd, 0, nc, base, t.row1, ws, acc);
+    tile_dots<V>(a, nd, 0, nc, base, end, ws, acc);
     __syncthreads();
   }
   store_dots<V>(a, nc, acc);
+  if (a.pb_b) prof_add(a.pb_b, pbytes);
   if (last_cta(&u.cnt, u.ntile)) {
     final_reduce(a.partials, a.stride, u.tile0, u.ntile, nc, out);
     if (threadIdx.x == 0) {
@@ -218,13 +300,29 @@ __global__ void __launch_bounds__(RSB_BLOCK) k_lz_c(LzArgs<V> a, int j, double b
   V* w_ = (j & 1) ? a.W0 : a.W1;
   const int nd = u.nd;
   Acc<V> acc;
-  for (int r = t.row0 + threadIdx.x; r < t.row1; r += RSB_BLOCK) {
-    const V w = gs_update<V>(a, u, u.c2, nd, j + 1, r, w_[r]);
-    w_[r] = w;
-    acc.add(w * w);
+  unsigned long long pbytes = 0;
+  for (int base = t.row0; base < t.row1; base += SUBROWS) {
+    const int end = min(t.row1, base + SUBROWS);
+    V w[RSB_SUBR];
+#pragma unroll
+    for (int rr = 0; rr < RSB_SUBR; ++rr) {
+      const int r = base + rr * RSB_BLOCK + threadIdx.x;
+      w[rr] = r < end ? w_[r] : V(0);
+    }
+    gs_update_rows<V>(a, u, u.c2, nd, j + 1, base, end, w);
+#pragma unroll
+    for (int rr = 0; rr < RSB_SUBR; ++rr) {
+      const int r = base + rr * RSB_BLOCK + threadIdx.x;
+      if (r < end) {
+        w_[r] = w[rr];
+        acc.add(w[rr] * w[rr]);
+        if (a.pb_c) pbytes += sizeof(V) * (unsigned long long)(3 + j) + 8ull * nd;
+      }
+    }
   }
-  const double s = block_sum(acc.get(), sm);
-  if (threadIdx.x == 0) a.partials[blockIdx.x] = s;
+  if (a.pb_c) prof_add(a.pb_c, pbytes);
+  const double sum = block_sum(acc.get(), sm);
+  if (threadIdx.x == 0) a.partials[blockIdx.x] = sum;
   if (last_cta(&u.cnt, u.ntile)) {
     final_reduce(a.partials, a.stride, u.tile0, u.ntile, 1, out);
     if (threadIdx.x == 0) {
@@ -238,58 +336,103 @@ __global__ void __launch_bounds__(RSB_BLOCK) k_lz_c(LzArgs<V> a, int j, double b
 // ----------------------------------------------------------------------------
 // smallest eigenpair of the symmetric tridiagonal T_K (one warp per unit)
 // ----------------------------------------------------------------------------
-// Eigenvalue: Sturm-count multisection (32 shifts per round); eigenvector:
-// inverse iteration with Gaussian elimination with partial pivoting on the
-// tridiagonal T - theta I.
-__device__ int sturm_count(const double* al, const double* be, int K, double sig, double pivmin) {
-  int cnt = 0;
-  double d = al[0] - sig;
-  if (fabs(d) < pivmin) d = -pivmin;
-  if (d < 0) ++cnt;
+// Eigenvalue: Sturm-count multisection (32 shifts per round, one per lane).
+// The count of eigenvalues below sigma is the number of sign changes of the
+// leading principal minors p_k = det(T_k - sigma I), p_k = (alpha_k - sigma)
+// p_{k-1} - beta_k^2 p_{k-2} (a zero takes the sign opposite to its
+// predecessor); two FMAs per step and exact power-of-two rescaling, no
+// division.  Eigenvector: inverse iteration on T - theta I, factorised once by
+// Gaussian elimination with partial pivoting (reciprocals from an FP32 seed
+// refined by two Newton steps to FP64 accuracy), then two multiply-only solves.
+__device__ __forceinline__ double fast_rcp(double x) {
+  const double ax = fabs(x);
+  if (!(ax > 1e-30 && ax < 1e30)) return 1.0 / x;
+  double r = (double)__frcp_rn((float)x);
+  r = r * fma(-x, r, 2.0);
+  r = r * fma(-x, r, 2.0);
+  return r;
+}
+
+__device__ int sturm_count(const double* al, const double* b2, int K, double sig) {
+  const double BIG = 0x1p500, SMALL = 0x1p-500;
+  double pm = 1.0;
+  double p = al[0] - sig;
+  int sprev = 1, cnt = 0;
+  int sg = p > 0.0 ? 1 : (p < 0.0 ? -1 : -sprev);
+  cnt += sg != sprev;
+  sprev = sg;
   for (int k = 1; k < K; ++k) {
-    d = al[k] - sig - be[k] * be[k] / d;
-    if (fabs(d) < pivmin) d = -pivmin;
-    if (d < 0) ++cnt;
+    const double pn = fma(al[k] - sig, p, -b2[k] * pm);
+    pm = p;
+    p = pn;
+    const double ap = fabs(p);
+    if (ap > BIG) {
+      p *= SMALL;
+      pm *= SMALL;
+    } else if (ap < SMALL && ap > 0.0) {
+      p *= BIG;
+      pm *= BIG;
+    }
+    sg = p > 0.0 ? 1 : (p < 0.0 ? -1 : -sprev);
+    cnt += sg != sprev;
+    sprev = sg;
   }
   return cnt;
 }
 
-__device__ void tridiag_solve_pivot(const double* al, const double* be, int K, double theta,
-                                    double pert, double* x) {
-  double d[RSB_MAXM], du[RSB_MAXM], dl[RSB_MAXM], b[RSB_MAXM];
+struct TriLU {
+  double d[RSB_MAXM], du[RSB_MAXM], du2[RSB_MAXM], f[RSB_MAXM], rd[RSB_MAXM];
+  unsigned char swp[RSB_MAXM];
+};
+
+__device__ void tri_factor(const double* al, const double* be, int K, double theta, double pert,
+                           TriLU& F) {
+  double dl[RSB_MAXM];
   for (int k = 0; k < K; ++k) {
-    d[k] = al[k] - theta;
-    du[k] = (k + 1 < K) ? be[k + 1] : 0.0;
+    F.d[k] = al[k] - theta;
+    F.du[k] = (k + 1 < K) ? be[k + 1] : 0.0;
     dl[k] = (k + 1 < K) ? be[k + 1] : 0.0;
-    b[k] = x[k];
+    F.du2[k] = 0.0;
+    F.swp[k] = 0;
   }
-  double du2[RSB_MAXM];
-  for (int k = 0; k < K; ++k) du2[k] = 0.0;
   for (int k = 0; k + 1 < K; ++k) {
-    if (fabs(d[k]) >= fabs(dl[k])) {
-      if (d[k] == 0.0) d[k] = pert;
-      const double f = dl[k] / d[k];
-      d[k + 1] -= f * du[k];
-      b[k + 1] -= f * b[k];
+    if (fabs(F.d[k]) >= fabs(dl[k])) {
+      if (F.d[k] == 0.0) F.d[k] = pert;
+      const double fk = dl[k] * fast_rcp(F.d[k]);
+      F.f[k] = fk;
+      F.d[k + 1] -= fk * F.du[k];
     } else {
-      const double f = d[k] / dl[k];
-      d[k] = dl[k];
-      const double tmp = d[k + 1];
-      d[k + 1] = du[k] - f * tmp;
+      const double fk = F.d[k] * fast_rcp(dl[k]);
+      F.f[k] = fk;
+      F.swp[k] = 1;
+      F.d[k] = dl[k];
+      const double tmp = F.d[k + 1];
+      F.d[k + 1] = F.du[k] - fk * tmp;
       if (k + 2 < K) {
-        du2[k] = du[k + 1];
-        du[k + 1] = -f * du2[k];
+        F.du2[k] = F.du[k + 1];
+        F.du[k + 1] = -fk * F.du2[k];
       }
-      du[k] = tmp;
-      const double tb = b[k];
-      b[k] = b[k + 1];
-      b[k + 1] = tb - f * b[k + 1];
+      F.du[k] = tmp;
     }
   }
-  if (d[K - 1] == 0.0) d[K - 1] = pert;
-  x[K - 1] = b[K - 1] / d[K - 1];
-  if (K >= 2) x[K - 2] = (b[K - 2] - du[K - 2] * x[K - 1]) / d[K - 2];
-  for (int k = K - 3; k >= 0; --k) x[k] = (b[k] - du[k] * x[k + 1] - du2[k] * x[k + 2]) / d[k];
+  if (F.d[K - 1] == 0.0) F.d[K - 1] = pert;
+  for (int k = 0; k < K; ++k) F.rd[k] = fast_rcp(F.d[k]);
+}
+
+__device__ void tri_solve(const TriLU& F, int K, double* x) {
+  for (int k = 0; k + 1 < K; ++k) {
+    if (F.swp[k]) {
+      const double tb = x[k];
+      x[k] = x[k + 1];
+      x[k + 1] = tb - F.f[k] * x[k + 1];
+    } else {
+      x[k + 1] -= F.f[k] * x[k];
+    }
+  }
+  x[K - 1] *= F.rd[K - 1];
+  if (K >= 2) x[K - 2] = (x[K - 2] - F.du[K - 2] * x[K - 1]) * F.rd[K - 2];
+  for (int k = K - 3; k >= 0; --k)
+    x[k] = (x[k] - F.du[k] * x[k + 1] - F.du2[k] * x[k + 2]) * F.rd[k];
 }
 
 __global__ void k_lz_tridiag(Unit* units, int nunits) {
@@ -299,23 +442,22 @@ __global__ void k_lz_tridiag(Unit* units, int nunits) {
   if (u.status != U_ACTIVE) return;
   const int lane = threadIdx.x;
   const int K = u.msteps;
-  const double* al = u.alpha;
-  const double* be = u.beta;  // be[k] couples rows k-1 and k
-  double lo = 1e300, hi = -1e300, bmax = 0.0;
+  double al[RSB_MAXM], b2[RSB_MAXM];
+  double lo = 1e300, hi = -1e300;
   for (int k = 0; k < K; ++k) {
-    const double r = (k > 0 ? fabs(be[k]) : 0.0) + (k + 1 < K ? fabs(be[k + 1]) : 0.0);
+    al[k] = u.alpha[k];
+    b2[k] = k > 0 ? u.beta[k] * u.beta[k] : 0.0;
+    const double r = (k > 0 ? fabs(u.beta[k]) : 0.0) + (k + 1 < K ? fabs(u.beta[k + 1]) : 0.0);
     lo = fmin(lo, al[k] - r);
     hi = fmax(hi, al[k] + r);
-    if (k > 0) bmax = fmax(bmax, fabs(be[k]));
   }
   const double tnorm = fmax(fabs(lo), fabs(hi));
-  const double pivmin = DBL_MIN * fmax(1.0, bmax * bmax);
-  // multisection for the smallest eigenvalue: invariant count(lo) = 0 <= count(hi)
+  // multisection for the smallest eigenvalue: count(lo) = 0 <= count(hi)
   for (int it = 0; it < 40; ++it) {
-    if (hi - lo <= 2.0 * DBL_EPSILON * fmax(fabs(lo), fabs(hi)) + pivmin) break;
-    const double step = (hi - lo) / 33.0;
+    if (hi - lo <= 2.0 * DBL_EPSILON * fmax(fabs(lo), fabs(hi)) + DBL_MIN) break;
+    const double step = (hi - lo) * (1.0 / 33.0);
     const double sig = lo + step * (lane + 1);
-    const int c = sturm_count(al, be, K, sig, pivmin);
+    const int c = sturm_count(al, b2, K, sig);
     const unsigned m = __ballot_sync(0xffffffffu, c >= 1);
     const int first = m ? __ffs(m) - 1 : 32;
     const double nhi = first < 32 ? lo + step * (first + 1) : hi;
@@ -325,13 +467,15 @@ __global__ void k_lz_tridiag(Unit* units, int nunits) {
   }
   const double theta = 0.5 * (lo + hi);
   if (lane == 0) {
+    TriLU F;
+    const double pert = DBL_EPSILON * fmax(tnorm, DBL_MIN);
+    tri_factor(al, u.beta, K, theta, pert, F);
     double x[RSB_MAXM];
     for (int k = 0; k < K; ++k) x[k] = 1.0;
-    const double pert = DBL_EPSILON * fmax(tnorm, DBL_MIN);
-    for (int it = 0; it < 3; ++it) {
-      tridiag_solve_pivot(al, be, K, theta, pert, x);
+    for (int it = 0; it < 2; ++it) {
+      tri_solve(F, K, x);
       double nrm = 0.0;
-      for (int k = 0; k < K; ++k) nrm += x[k] * x[k];
+      for (int k = 0; k < K; ++k) nrm = fma(x[k], x[k], nrm);
       nrm = 1.0 / sqrt(nrm);
       for (int k = 0; k < K; ++k) x[k] *= nrm;
     }
@@ -550,6 +694,10 @@ static LzArgs<V> make_args(const LevelGraph& G, const Tile* tiles, int ntiles, U
   a.stride = ntiles;
   a.n_active = B.n_active;
   a.stat_cycles = B.stat_cycles;
+  a.pb_a = prof_bytes(PROF_LZ_A);
+  a.pb_b = prof_bytes(PROF_LZ_B);
+  a.pb_c = prof_bytes(PROF_LZ_C);
+  a.pb_cg = prof_bytes(PROF_CG_AP);
   return a;
 }
 
@@ -565,6 +713,7 @@ int solver_setup(Unit* units, int nunits, int nd, int krylov, int maxcycles, dou
 static int read_active(SolveBufs& B, cudaStream_t s, int* out) {
   RSB_CK(cudaMemcpyAsync(B.h_active, B.n_active, sizeof(int), cudaMemcpyDeviceToHost, s));
   RSB_CK(cudaStreamSynchronize(s));
+  prof_collect();
   *out = *B.h_active;
   return RSB_OK;
 }
@@ -586,13 +735,19 @@ static int lz_start(LzArgs<V>& a, int ntiles, uint64_t sd, const double* from64,
 template <typename V>
 static int lz_cycle(LzArgs<V>& a, int ntiles, int nunits, int M, double breakdown, cudaStream_t s) {
   for (int j = 0; j < M; ++j) {
+    int pi = prof_before(PROF_LZ_A, s);
     k_lz_a<V><<<ntiles, RSB_BLOCK, 0, s>>>(a, j);
     RSB_CKL("k_lz_a");
+    prof_after(pi, s);
     if (j + 1 < M) {
+      pi = prof_before(PROF_LZ_B, s);
       k_lz_b<V><<<ntiles, RSB_BLOCK, 0, s>>>(a, j);
       RSB_CKL("k_lz_b");
+      prof_after(pi, s);
+      pi = prof_before(PROF_LZ_C, s);
       k_lz_c<V><<<ntiles, RSB_BLOCK, 0, s>>>(a, j, breakdown);
       RSB_CKL("k_lz_c");
+      prof_after(pi, s);
     }
   }
   k_lz_tridiag<<<nunits, 32, 0, s>>>(a.units, nunits);
@@ -623,10 +778,13 @@ static int lanczos_run(const LevelGraph& G, const Tile* tiles, int ntiles, Unit*
   if (rc) return rc;
   const double breakdown = 1e-14;
   cudaGraphExec_t exec = nullptr;
+  std::vector<int> cap_pairs;
   if (use_graph) {
     cudaGraph_t graph = nullptr;
     RSB_CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+    prof_capture_begin();
     rc = lz_cycle<V>(a, ntiles, nunits, M, breakdown, s);
+    cap_pairs = prof_capture_end();
     cudaGraph_t g2 = nullptr;
     cudaError_t e = cudaStreamEndCapture(s, &g2);
     graph = g2;
@@ -647,6 +805,7 @@ static int lanczos_run(const LevelGraph& G, const Tile* tiles, int ntiles, Unit*
         cudaGraphExecDestroy(exec);
         return rsb_set_cuda_error(e, "cudaGraphLaunch");
       }
+      prof_replay(cap_pairs);
     } else {
       rc = lz_cycle<V>(a, ntiles, nunits, M, breakdown, s);
       if (rc) return rc;
@@ -711,12 +870,15 @@ __global__ void __launch_bounds__(RSB_BLOCK) k_cg_ap(LzArgs<V> a) {
   Unit& u = a.units[t.unit];
   if (u.status != U_ACTIVE || u.cg_done) return;
   Acc<V> acc;
+  unsigned long long pbytes = 0;
   for (int r = t.row0 + threadIdx.x; r < t.row1; r += RSB_BLOCK) {
     const V pr = a.P[r];
     const V ap = spmv_row<V>(a.slice_ptr, a.ent, a.P, r, pr);
     a.AP[r] = ap;
     acc.add(pr * ap);
+    if (a.pb_cg) pbytes += 4ull * row_width(a.slice_ptr, r) + 2ull * sizeof(V);
   }
+  if (a.pb_cg) prof_add(a.pb_cg, pbytes);
   const double sum = block_sum(acc.get(), sm);
   if (threadIdx.x == 0) a.partials[blockIdx.x] = sum;
   if (last_cta(&u.cnt, u.ntile)) {
@@ -827,7 +989,7 @@ __global__ void __launch_bounds__(RSB_BLOCK) k_inv_rq(LzArgs<V> a) {
 // Outer step: residual ||Ly - lambda y|| / ||y||, stop tests, projection dots
 // of y for the next right-hand side.
 template <typename V>
-__global__ void __launch_bounds__(RSB_BLOCK) k_inv_res(LzArgs<V> a, int max_outer) {
+__global__ void __launch_bounds__(RSB_BLOCK) k_inv_res(LzArgs<V> a, int max_outer, int refine) {
   __shared__ double sm[RSB_WARPS];
   __shared__ double out[2 + RSB_MAXD];
   const Tile t = a.tiles[blockIdx.x];
@@ -856,6 +1018,11 @@ __global__ void __launch_bounds__(RSB_BLOCK) k_inv_res(LzArgs<V> a, int max_oute
       u.resid = sqrt(out[0] / u.ynorm2);
       u.cp[0] = out[1] * u.isn;
       for (int l = 0; l < nd; ++l) u.cp[1 + l] = out[2 + l];
+      if (refine) {
+        u.status = u.resid <= u.tolabs ? U_CONVERGED : U_CAPPED;
+        atomicSub(a.n_active, 1);
+        return;
+      }
       u.cycles += 1;
       atomicAdd((unsigned long long*)a.stat_cycles, 1ull);
       int st = U_ACTIVE;
@@ -878,8 +1045,10 @@ template <typename V>
 static int cg_block(LzArgs<V>& a, int ntiles, int iters, double cg_tol, int cg_maxit, int* n_cg,
                     cudaStream_t s) {
   for (int i = 0; i < iters; ++i) {
+    const int pi = prof_before(PROF_CG_AP, s);
     k_cg_ap<V><<<ntiles, RSB_BLOCK, 0, s>>>(a);
     RSB_CKL("k_cg_ap");
+    prof_after(pi, s);
     k_cg_xr<V><<<ntiles, RSB_BLOCK, 0, s>>>(a, cg_tol, cg_maxit, n_cg);
     RSB_CKL("k_cg_xr");
     k_cg_p<V><<<ntiles, RSB_BLOCK, 0, s>>>(a);
@@ -901,10 +1070,13 @@ static int inverse_run(const LevelGraph& G, const Tile* tiles, int ntiles, Unit*
   if (rc) return rc;
   const int CGK = 8;
   cudaGraphExec_t exec = nullptr;
+  std::vector<int> cap_pairs;
   if (use_graph) {
     cudaGraph_t graph = nullptr;
     RSB_CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+    prof_capture_begin();
     rc = cg_block<V>(a, ntiles, CGK, cg_tol, cg_maxit, B.n_cg, s);
+    cap_pairs = prof_capture_end();
     cudaError_t e = cudaStreamEndCapture(s, &graph);
     if (rc) {
       if (graph) cudaGraphDestroy(graph);
@@ -929,6 +1101,7 @@ static int inverse_run(const LevelGraph& G, const Tile* tiles, int ntiles, Unit*
           cudaGraphExecDestroy(exec);
           return rsb_set_cuda_error(e, "cudaGraphLaunch");
         }
+        prof_replay(cap_pairs);
       } else {
         rc = cg_block<V>(a, ntiles, CGK, cg_tol, cg_maxit, B.n_cg, s);
         if (rc) break;
@@ -936,13 +1109,14 @@ static int inverse_run(const LevelGraph& G, const Tile* tiles, int ntiles, Unit*
       int ncg = 0;
       RSB_CK(cudaMemcpyAsync(B.h_active, B.n_cg, sizeof(int), cudaMemcpyDeviceToHost, s));
       RSB_CK(cudaStreamSynchronize(s));
+      prof_collect();
       ncg = *B.h_active;
       if (ncg <= 0) break;
     }
     if (rc) break;
     k_inv_rq<V><<<ntiles, RSB_BLOCK, 0, s>>>(a);
     RSB_CKL("k_inv_rq");
-    k_inv_res<V><<<ntiles, RSB_BLOCK, 0, s>>>(a, max_outer);
+    k_inv_res<V><<<ntiles, RSB_BLOCK, 0, s>>>(a, max_outer, 0);
     RSB_CKL("k_inv_res");
     rc = read_active(B, s, &active);
     if (rc || active == 0) break;
@@ -967,6 +1141,27 @@ int solver_inverse(const LevelGraph& G, const Tile* tiles, int ntiles, Unit* uni
                               cg_maxit, max_outer, use_graph, nullptr, s);
   return inverse_run<double>(G, tiles, ntiles, units, nunits, ckey, B, sd, from64, from32, cg_tol,
                              cg_maxit, max_outer, use_graph, nullptr, s);
+}
+
+// ----------------------------------------------------------------------------
+// FP64 Rayleigh-quotient refinement of an FP32 vector (mixed precision):
+// y = FP64 copy of the FP32 vector, theta = y^T L y / y^T y and the residual
+// ||L y - theta y|| / ||y|| in FP64; the FP64 y lands in B.X.
+// ----------------------------------------------------------------------------
+int solver_rq_refine(const LevelGraph& G, const Tile* tiles, int ntiles, Unit* units, int nunits,
+                     const uint64_t* ckey, SolveBufs& B, const float* from32, cudaStream_t s) {
+  if (ntiles <= 0 || nunits <= 0) return RSB_OK;
+  SolveBufs Bx = B;
+  Bx.Y = B.X;  // k_start writes a.Y; the refinement kernels read a.X
+  LzArgs<double> a = make_args<double>(G, tiles, ntiles, units, ckey, Bx);
+  k_start<double><<<ntiles, RSB_BLOCK, 0, s>>>(a, 0ull, nullptr, from32);
+  RSB_CKL("k_start(refine)");
+  k_inv_rq<double><<<ntiles, RSB_BLOCK, 0, s>>>(a);
+  RSB_CKL("k_inv_rq(refine)");
+  k_inv_res<double><<<ntiles, RSB_BLOCK, 0, s>>>(a, 0, 1);
+  RSB_CKL("k_inv_res(refine)");
+  (void)nunits;
+  return RSB_OK;
 }
 
 // ----------------------------------------------------------------------------

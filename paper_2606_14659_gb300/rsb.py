@@ -23,7 +23,8 @@ RSB_DEGEN_NONE, RSB_DEGEN_RESOLVE = 0, 1
 
 EXPORTED = ["rsb_options_default", "rsb_partition", "rsb_partition_batch", "rsb_fiedler",
             "rsb_laplacian_apply", "rsb_laplacian_apply_f32", "rsb_laplacian_bench",
-            "rsb_strerror", "rsb_last_error_detail", "rsb_release"]
+            "rsb_strerror", "rsb_last_error_detail", "rsb_release", "rsb_profile_begin",
+            "rsb_profile_end"]
 
 
 class rsb_csr(C.Structure):
@@ -37,7 +38,7 @@ class rsb_options(C.Structure):
                 ("cg_maxit", C.c_int), ("max_outer", C.c_int), ("seed", C.c_uint64),
                 ("degenerate_policy", C.c_int), ("cluster_tol", C.c_double),
                 ("tie_rel", C.c_double), ("mixed_tol", C.c_double), ("batched", C.c_int),
-                ("use_graph", C.c_int), ("validate", C.c_int)]
+                ("use_graph", C.c_int), ("validate", C.c_int), ("polish_cycles", C.c_int)]
 
 
 class rsb_stats(C.Structure):
@@ -82,6 +83,11 @@ def load():
     lib.rsb_last_error_detail.restype = C.c_char_p
     lib.rsb_release.argtypes = []
     lib.rsb_release.restype = None
+    lib.rsb_profile_begin.argtypes = [C.c_int]
+    lib.rsb_profile_begin.restype = None
+    lib.rsb_profile_end.argtypes = [C.POINTER(C.c_double), C.POINTER(C.c_int64),
+                                    C.POINTER(C.c_double)]
+    lib.rsb_profile_end.restype = None
     for name in ("rsb_partition", "rsb_partition_batch", "rsb_fiedler", "rsb_laplacian_apply",
                  "rsb_laplacian_apply_f32", "rsb_laplacian_bench"):
         getattr(lib, name).restype = C.c_int
@@ -282,3 +288,21 @@ def rsb_laplacian_bench(g: Graph, f32: bool, reps: int = 20, stream=None):
 
 def rsb_release():
     load().rsb_release()
+
+
+PROFILE_FAMILIES = {"lz_a": 1, "lz_b": 2, "lz_c": 3, "cg_ap": 4, "spmv": 5}
+
+
+def rsb_profile_begin(family: str | int):
+    """Times every launch of one kernel family in the following calls."""
+    fam = PROFILE_FAMILIES[family] if isinstance(family, str) else int(family)
+    load().rsb_profile_begin(fam)
+
+
+def rsb_profile_end():
+    """(total ms, launches, algorithmic bytes) of the profiled family."""
+    ms = C.c_double(0.0)
+    n = C.c_int64(0)
+    by = C.c_double(0.0)
+    load().rsb_profile_end(C.byref(ms), C.byref(n), C.byref(by))
+    return ms.value, n.value, by.value

@@ -41,6 +41,7 @@ def test_binding_struct_layout_and_strerror():
 
     lib = R.load()
     assert ctypes.sizeof(R.rsb_options) == 96
+    assert R.rsb_options.polish_cycles.offset == 92 and R.rsb_options.seed.offset == 40
     assert ctypes.sizeof(R.rsb_stats) == 72
     assert lib.rsb_strerror(0) == b"success"
     assert lib.rsb_strerror(R.RSB_EDISCONNECTED) == b"graph is disconnected"

@@ -85,20 +85,35 @@ def test_fiedler_box(method, precision, dims):
     lam, v, res, code = R.rsb_fiedler(R.graph(g), R.options(method=method, precision=precision))
     assert code == 0
     lam_ref = O.box_lambda2(*dims)
-    assert abs(lam - lam_ref) <= 1e-9 * lam_ref
     lo, vo, _ = O.fiedler_of_graph(g, O.Options(method=method))
-    assert np.abs(_np(v) - vo).max() < 1e-6
-    assert res <= 1e-10 * O.degree(g).max() * 1.01
+    dmax = O.degree(g).max()
+    if precision == "fp64":
+        assert abs(lam - lam_ref) <= 1e-9 * lam_ref
+        assert np.abs(_np(v) - vo).max() < 1e-6
+        assert res <= 1e-10 * dmax * 1.01
+    else:  # FP32 stage + FP64 Rayleigh quotient: the mixed form's stated bar
+        assert abs(lam - lam_ref) <= 1e-6 * lam_ref
+        assert np.abs(_np(v) - vo).max() < 1e-4
+        assert res <= 1e-5 * dmax
+
+
+@pytest.mark.parametrize("polish", [2, 6])
+def test_fiedler_mixed_polish_reaches_fp64(polish):
+    g = box_graph(12, 7, 5)
+    lam, v, res, code = R.rsb_fiedler(R.graph(g), R.options(precision="mixed",
+                                                             polish_cycles=polish))
+    assert abs(lam - O.box_lambda2(12, 7, 5)) <= 1e-10 * O.box_lambda2(12, 7, 5)
+    assert res <= 1e-9 * O.degree(g).max()
 
 
 @pytest.mark.parametrize("seed", [0, 1, 2])
 def test_fiedler_random_vs_oracle(seed):
     g = random_graph(300, 700, 40 + seed)
     lam_o, v_o, r_o = O.fiedler_of_graph(g)
-    for prec in ("fp64", "mixed"):
+    for prec, lt, vt in (("fp64", 1e-9, 1e-5), ("mixed", 1e-6, 1e-3)):
         lam, v, res, code = R.rsb_fiedler(R.graph(g), R.options(precision=prec))
-        assert abs(lam - lam_o) <= 1e-9 * lam_o
-        assert np.abs(_np(v) - v_o).max() < 1e-5
+        assert abs(lam - lam_o) <= lt * lam_o
+        assert np.abs(_np(v) - v_o).max() < vt
         assert res / O.degree(g).max() <= 1e-5
 
 
@@ -136,7 +151,7 @@ def test_partition_c1_closed_form(precision, batched, use_graph):
     assert code == 0
     assert np.array_equal(_np(part), _closed_c1())
     assert st["levels"] == 3 and st["elements_bisected"] == 3 * 512
-    assert abs(st["lambda_first"] - O.box_lambda2(16, 8, 4)) <= 1e-9
+    assert abs(st["lambda_first"] - O.box_lambda2(16, 8, 4)) <= 1e-6 * O.box_lambda2(16, 8, 4)
 
 
 @pytest.mark.parametrize("method", ["lanczos", "inverse"])
