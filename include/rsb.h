@@ -185,6 +185,28 @@ int rsb_laplacian_apply_f32(const rsb_csr *g, const float *x, float *y, void *st
 int rsb_laplacian_bench(const rsb_csr *g, int f32, int reps, double *ms_per_apply,
                         double *useful_bytes, void *stream);
 
+/*
+ * rsb_laplacian_apply_noalloc — y = L x (FP64) like rsb_laplacian_apply, for
+ * callers that cannot allocate device memory.  The paper has no counterpart;
+ * this is a deployment variant.  Some callers must not call cudaMalloc: code
+ * running while a framework's caching allocator holds the whole device, code
+ * in a region where the implicit synchronisation of cudaMalloc/cudaFree is not
+ * allowed, or embedders that budget every device byte up front.  This call
+ * allocates nothing: its scratch (the sliced-ELL copy of g and a scan
+ * workspace) lives in one 32 MiB device array compiled into the library, which
+ * every GPU that loads the library holds until the process exits.
+ *   g, x, y  device pointers only (RSB_EINVAL otherwise); x, y double[n]
+ *   stream   used directly; the call returns after the result is on it
+ * Graphs whose scratch exceeds the 32 MiB (about 4 B per padded SELL entry
+ * plus 28 B per row) are rejected with RSB_EINVAL.  All calls share the array
+ * and leave their contents in it; each call clears what must start at zero.
+ * Calls that overlap on the GPU (other streams or host threads) race on the
+ * array: order them.  The first call on each device looks up the array's
+ * device address (cudaGetSymbolAddress, that device current); make it before
+ * any stream capture.
+ */
+int rsb_laplacian_apply_noalloc(const rsb_csr *g, const double *x, double *y, void *stream);
+
 /* Static description of an error code. */
 const char *rsb_strerror(int code);
 

@@ -24,7 +24,7 @@ RSB_DEGEN_NONE, RSB_DEGEN_RESOLVE = 0, 1
 EXPORTED = ["rsb_options_default", "rsb_partition", "rsb_partition_batch", "rsb_fiedler",
             "rsb_laplacian_apply", "rsb_laplacian_apply_f32", "rsb_laplacian_bench",
             "rsb_strerror", "rsb_last_error_detail", "rsb_release", "rsb_profile_begin",
-            "rsb_profile_end"]
+            "rsb_profile_end", "rsb_laplacian_apply_noalloc"]
 
 
 class rsb_csr(C.Structure):
@@ -75,6 +75,7 @@ def load():
                                 C.POINTER(C.c_double), vp, C.POINTER(C.c_double), vp]
     lib.rsb_laplacian_apply.argtypes = [C.POINTER(rsb_csr), vp, vp, vp]
     lib.rsb_laplacian_apply_f32.argtypes = [C.POINTER(rsb_csr), vp, vp, vp]
+    lib.rsb_laplacian_apply_noalloc.argtypes = [C.POINTER(rsb_csr), vp, vp, vp]
     lib.rsb_laplacian_bench.argtypes = [C.POINTER(rsb_csr), C.c_int, C.c_int,
                                         C.POINTER(C.c_double), C.POINTER(C.c_double), vp]
     lib.rsb_strerror.argtypes = [C.c_int]
@@ -89,7 +90,7 @@ def load():
                                     C.POINTER(C.c_double)]
     lib.rsb_profile_end.restype = None
     for name in ("rsb_partition", "rsb_partition_batch", "rsb_fiedler", "rsb_laplacian_apply",
-                 "rsb_laplacian_apply_f32", "rsb_laplacian_bench"):
+                 "rsb_laplacian_apply_f32", "rsb_laplacian_bench", "rsb_laplacian_apply_noalloc"):
         getattr(lib, name).restype = C.c_int
     _lib = lib
     return lib
@@ -273,6 +274,13 @@ def rsb_laplacian_apply(g: Graph, x, y=None, stream=None):
     fn = lib.rsb_laplacian_apply_f32 if f32 else lib.rsb_laplacian_apply
     _check(fn(C.byref(cs), _ptr(x), _ptr(y), _stream(stream)), "rsb_laplacian_apply")
     return y
+
+
+def rsb_laplacian_apply_noalloc(g: Graph, x, y, stream=None):
+    """y = L x (FP64, device tensors) without any device allocation in the library."""
+    lib = load()
+    cs = g.c_struct()
+    return lib.rsb_laplacian_apply_noalloc(C.byref(cs), _ptr(x), _ptr(y), _stream(stream))
 
 
 def rsb_laplacian_bench(g: Graph, f32: bool, reps: int = 20, stream=None):
