@@ -3,8 +3,9 @@
 Default workload: the 64x64x32 box hex mesh (131,072 elements), face-adjacency
 dual graph with unit weights, bisected to 64 parts (6 levels) by Lanczos in
 mixed precision (FP32 vectors, FP64 coefficients / tridiagonal / Rayleigh
-quotient), every level's subgraphs batched in one set of launches, Lanczos
-cycles replayed as CUDA graphs.  A step is one full rsb_partition call from
+quotient), every level's subgraphs batched in one set of launches, each
+Lanczos cycle replayed as one CUDA graph (--launch 2: one persistent
+cooperative kernel per cycle).  A step is one full rsb_partition call from
 device-resident CSR to part ids.  metric = (sum over levels and split
 segments of their element count) / time.
 
@@ -174,6 +175,26 @@ class Clocks:
 
 
 # ----------------------------------------------------------------------------
+# multi-rank aggregation: independent replicas, one number for the job
+# ----------------------------------------------------------------------------
+def aggregate(total_ms: float, units: float, dist=None, device=None):
+    """(slowest rank's time in ms, units of all ranks).
+
+    Weak scaling: every rank runs the same workload on its own GPU; the job's
+    throughput is all ranks' units over the slowest rank's time.
+    """
+    if dist is None or not dist.is_initialized() or dist.get_world_size() == 1:
+        return float(total_ms), float(units)
+    import torch
+
+    t = torch.tensor([float(total_ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    u = torch.tensor([float(units)], dtype=torch.float64, device=device)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(u.item())
+
+
+# ----------------------------------------------------------------------------
 # our arm
 # ----------------------------------------------------------------------------
 WORKLOAD_NAME = ("box 64x64x32 hex mesh, face-adjacency dual graph, unit weights, "
@@ -200,7 +221,7 @@ def our_arm(args):
     P = W["parts"]
     G = R.graph(g, device=f"cuda:{local}")
     opts = R.options(method=W["method"], precision=args.precision, degenerate_policy=W["degenerate"],
-                     batched=1, use_graph=1)
+                     batched=1, use_graph=args.launch)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=f"cuda:{local}")
     out = torch.empty(g.n, dtype=torch.int32, device=f"cuda:{local}")
 
@@ -218,7 +239,6 @@ def our_arm(args):
         dist.barrier()
     torch.cuda.synchronize()
     clocks.start()
-    R.rsb_profile_begin(fam)
     for _ in range(args.steps):
         flush.zero_()
         e0 = torch.cuda.Event(enable_timing=True)
@@ -230,21 +250,25 @@ def our_arm(args):
         ms_steps.append(e0.elapsed_time(e1))
         units += st["elements_bisected"]
         launches += st["kernel_launches"]
-    prof_ms, prof_launches, prof_bytes = R.rsb_profile_end()
     torch.cuda.synchronize()
     clk = clocks.stop()
     if dist is not None:
         dist.barrier()
-    total_ms = sum(ms_steps)
-    if dist is not None:
-        t = torch.tensor([total_ms], dtype=torch.float64, device=f"cuda:{local}")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-        u = torch.tensor([units], dtype=torch.float64, device=f"cuda:{local}")
-        dist.all_reduce(u, op=dist.ReduceOp.SUM)
-        units_all = float(u.item())
-    else:
-        units_all = units
+    # the same steps again with the dominant kernel family bracketed by CUDA
+    # events (kept out of the headline timing: the event records add time)
+    prof_ms_steps = []
+    R.rsb_profile_begin(fam)
+    for _ in range(args.steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        step()
+        e1.record()
+        e1.synchronize()
+        prof_ms_steps.append(e0.elapsed_time(e1))
+    prof_ms, prof_launches, prof_bytes = R.rsb_profile_end()
+    total_ms, units_all = aggregate(sum(ms_steps), units, dist, f"cuda:{local}")
     value = units_all / (total_ms / 1e3)
     # correctness of what was timed (outside the timed region)
     from oracle import box_partition_closed_form  # noqa: WPS433  (check only)
@@ -277,7 +301,8 @@ def our_arm(args):
         # FP64 forms of the same workload (the mixed batched form must beat them)
         for name, kw in (("fp64_batched", dict(precision="fp64", batched=1)),
                          ("fp64_plain", dict(precision="fp64", batched=0))):
-            o2 = R.options(method=W["method"], degenerate_policy=W["degenerate"], use_graph=1, **kw)
+            o2 = R.options(method=W["method"], degenerate_policy=W["degenerate"],
+                           use_graph=args.launch, **kw)
             R.rsb_partition(G, P, o2, out=out)
             torch.cuda.synchronize()
             e0 = torch.cuda.Event(enable_timing=True)
@@ -308,16 +333,21 @@ def our_arm(args):
         "dtype": "f32/f64" if args.precision == "mixed" else "f64",
         "data": "synthetic",
         "config": {"workload": WORKLOAD_NAME, "method": W["method"], "precision": args.precision,
-                   "batched": True, "cuda_graphs": True, "elements": g.n, "parts": P,
+                   "batched": True, "launch": ["kernels", "cuda_graph", "persistent"][args.launch], "elements": g.n, "parts": P,
                    "l2": "flushed between steps (256 MiB write)", "matches_closed_form": ok},
         "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": launches,
-        "roofline": {"bound": "hbm", "kernel": f"lanczos step family '{fam}'",
+        "roofline": {"bound": "hbm",
+                     "kernel": ("k_lz_cycle<float> (persistent cooperative Lanczos cycle: SpMV, "
+                                "CGS2, tridiagonal, Ritz, residual, restart)") if fam == "cycle"
+                     else f"lanczos kernel family '{fam}'",
                      "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak if peak else None, "traffic": None,
                      "peak_kind": peak_kind, "launches_timed": prof_launches,
-                     "avg_launch_us": 1e3 * prof_ms / prof_launches if prof_launches else None},
+                     "avg_launch_us": 1e3 * prof_ms / prof_launches if prof_launches else None,
+                     "share_of_step": prof_ms / sum(prof_ms_steps) if prof_ms_steps else None,
+                     "timed_in": "profiled repeat of the timed steps (same workload and options)"},
         "clocks": clk,
     }
     line.update(extra)
@@ -348,7 +378,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="c2", choices=sorted(WORKLOADS))
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
-    ap.add_argument("--profile", default="lz_a", choices=["lz_a", "lz_b", "lz_c", "cg_ap"])
+    ap.add_argument("--profile", default="lz_b", choices=["cycle", "lz_a", "lz_b", "lz_c", "cg_ap"])
+    ap.add_argument("--launch", type=int, default=1, choices=[0, 1, 2],
+                    help="Lanczos cycle launch mode: 0 kernels, 1 CUDA graph, 2 persistent kernel")
     ap.add_argument("--quick", action="store_true", help="skip the FP64/SpMV/CPU extras")
     args = ap.parse_args()
     if args.impl == "reference":

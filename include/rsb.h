@@ -89,10 +89,16 @@ typedef struct rsb_options {
   double tie_rel;        /* median-split tie window, relative to the value range   */
   double mixed_tol;      /* MIXED: FP32 stage stops at max(tol, mixed_tol)         */
   int batched;           /* 1: all subgraphs of a level in one set of launches     */
-  int use_graph;         /* 1: capture each Lanczos cycle / CG block in a CUDA graph */
+  int use_graph;         /* launch mode of a Lanczos cycle: 0 one launch per kernel,
+                            1 one CUDA graph per cycle, 2 one persistent cooperative
+                            kernel per cycle (CG blocks use a CUDA graph for 1 and 2) */
   int validate;          /* 1: also check symmetry of the input on the device      */
   int polish_cycles;     /* MIXED: FP64 Lanczos cycles after the FP32 stage (0: only
                             the FP64 Rayleigh-quotient refinement of the FP32 vector) */
+  int keep;              /* Ritz vectors kept by a thick restart, 0..16 (0: restart
+                            from the Ritz vector alone)                               */
+  int tile_rows;         /* rows per thread of a solver tile (a tile is 256 x this
+                            many rows of one subgraph), 1..64; 0: the default 2     */
 } rsb_options;
 
 typedef struct rsb_stats {
@@ -111,7 +117,7 @@ typedef struct rsb_stats {
 /* Fills *o with the defaults: Lanczos, FP64, krylov_dim 40, max_restarts 50,
  * tol 1e-10, cg_tol 1e-12, cg_maxit 4000, max_outer 50, RESOLVE,
  * cluster_tol 0.05, tie_rel 1e-5, mixed_tol 1e-6, batched 1, use_graph 1,
- * validate 0, polish_cycles 0. */
+ * validate 0, polish_cycles 0, keep 8, tile_rows 0. */
 void rsb_options_default(rsb_options *o);
 
 /*
@@ -121,7 +127,8 @@ void rsb_options_default(rsb_options *o);
  * algorithmic bytes of each launch; rsb_profile_end() returns the totals and
  * switches timing off.  family: 1 Lanczos step A (SpMV + first Gram-Schmidt
  * dots), 2 step B (update + second dots), 3 step C (update + norm), 4 CG
- * Laplacian action, 5 Laplacian action of rsb_laplacian_bench.
+ * Laplacian action, 5 Laplacian action of rsb_laplacian_bench, 6 the
+ * persistent Lanczos-cycle kernel (bytes of its A, B and C phases).
  * Bytes count 4 B per stored SELL entry (padding included), every vector
  * element read or written once, and FP64 deflation vectors.
  */

@@ -27,12 +27,20 @@ R1  balance: part sizes differ by at most one (§2 prints "= 1").
 R2  recursion acts on the induced subgraph of each half; degrees are
     recomputed from the surviving edges.
 R3  Lanczos: Krylov length m = min(krylov_dim, n - 1 - #deflation vectors);
-    full re-orthogonalisation by two classical Gram-Schmidt passes against
-    [1/sqrt(n), deflation vectors, q_1..q_j] with alpha_j taken as the first
-    pass's coefficient on q_j; explicit restart from the normalised Ritz vector;
-    stop when ||L y - theta y|| <= tol * d_max (d_max = largest weighted degree,
-    a lower bound of ||L||_2), at most max_restarts cycles; a cycle ends early
-    when beta <= 1e-14 * d_max (invariant subspace).  Start vector:
+    each step takes w = L q_j and re-orthogonalises it fully by two classical
+    Gram-Schmidt passes against [1/sqrt(n), deflation vectors, q_0..q_j]; the
+    two passes' coefficients on q_0..q_j form column j of the projected matrix
+    S = Q^T L Q (tridiagonal in the first cycle, arrow-plus-tridiagonal after
+    a restart), beta_{j+1} = ||w||, q_{j+1} = w / beta_{j+1}.  At the end of a
+    cycle the Ritz pairs of S give theta (smallest) and y = Q s_1; the cycle is
+    thick-restarted (Wu & Simon, cited in §6): the `keep` smallest Ritz
+    vectors and the last residual direction w / beta_m are the first keep + 1
+    basis vectors of the next cycle, S restarts as diag(theta_1..theta_keep)
+    and the next m - keep steps add its new columns.  Stop when
+    ||L y - theta y|| <= tol * d_max (d_max = largest weighted degree, a lower
+    bound of ||L||_2), at most max_restarts cycles; a cycle ends early when
+    beta <= 1e-14 * d_max (invariant subspace; a cycle that ends that way and
+    has not converged restarts from y alone).  Start vector:
     s_i = 2 * (SplitMix64(s_d XOR gid_i) >> 11) * 2^-53 - 1 with
     s_d = SplitMix64(seed + d) for a solve deflated against d vectors, then
     projected and normalised (two classical Gram-Schmidt passes against the
@@ -84,6 +92,7 @@ import numpy as np
 class Options:
     method: str = "lanczos"          # "lanczos" | "inverse"
     krylov_dim: int = 40
+    keep: int = 8                    # Ritz vectors kept by a thick restart
     max_restarts: int = 50           # §8: the paper's cap of 50 restarts
     tol: float = 1e-10
     cg_tol: float = 1e-12
@@ -289,7 +298,7 @@ def tridiag_min_eigpair(alpha, beta):
 
 
 def lanczos_fiedler(g, opts: Options, deflate=(), start=None):
-    """Fiedler pair of a connected graph by restarted Lanczos (§6, reading R3).
+    """Fiedler pair of a connected graph by thick-restarted Lanczos (§6, reading R3).
 
     Returns None when the space orthogonal to 1 and `deflate` is empty.
     """
@@ -300,40 +309,49 @@ def lanczos_fiedler(g, opts: Options, deflate=(), start=None):
         return None
     m = min(opts.krylov_dim, dim)
     B = _fixed_basis(n, deflate)
+    nb = B.shape[1]
     dmax = float(degree(g).max())
     q = start_vector(g.gid, opts.seed, nd) if start is None else np.array(start, dtype=np.float64)
-    q = _project_start(B, q)
-    theta, y, res = 0.0, q, np.inf
-    # basis columns: [fixed basis B | q_1 .. q_m]
-    W = np.zeros((n, B.shape[1] + m))
-    W[:, :B.shape[1]] = B
-    nb = B.shape[1]
+    V = np.zeros((n, m))
+    S = np.zeros((m, m))
+    V[:, 0] = _project_start(B, q)
+    j0 = 0
+    theta, y, res = 0.0, V[:, 0], np.inf
     for cycle in range(1, opts.max_restarts + 1):
-        W[:, nb] = q
-        alpha, beta = [], []
-        for j in range(m):
-            w = laplacian_apply(g, W[:, nb + j])
-            if j > 0:
-                w = w - beta[j - 1] * W[:, nb + j - 1]
-            basis = W[:, :nb + j + 1]
+        meff, w_last = m, None
+        for j in range(j0, m):
+            w = laplacian_apply(g, V[:, j])
+            basis = np.concatenate([B, V[:, :j + 1]], axis=1)
             w, c1 = _cgs(basis, w)
-            alpha.append(float(c1[-1]))
-            if j == m - 1:
-                break
-            w, _ = _cgs(basis, w)
+            w, c2 = _cgs(basis, w)
+            col = (c1 + c2)[nb:]
+            S[:j + 1, j] = col
+            S[j, :j + 1] = col
             b = float(np.linalg.norm(w))
             if b <= opts.breakdown * dmax:
+                meff, w_last = j + 1, None
                 break
-            beta.append(b)
-            W[:, nb + j + 1] = w / b
-        k = len(alpha)
-        theta, t = tridiag_min_eigpair(alpha, beta)
-        y = W[:, nb:nb + k] @ t
+            if j + 1 < m:
+                V[:, j + 1] = w / b
+            else:
+                w_last = w / b
+        thetas, Y = np.linalg.eigh(S[:meff, :meff])
+        theta = float(thetas[0])
+        y = V[:, :meff] @ Y[:, 0]
         y = y / np.linalg.norm(y)
         res = float(np.linalg.norm(laplacian_apply(g, y) - theta * y))
         if res <= opts.tol * dmax:
             return FiedlerResult(theta, y, res, cycle, True)
-        q = _project_start(B, y)
+        k = min(opts.keep, meff - 1) if w_last is not None else 0
+        S[:] = 0.0
+        if k <= 0:
+            V[:, 0] = _project_start(B, y)
+            j0 = 0
+            continue
+        V[:, :k] = V[:, :meff] @ Y[:, :k]
+        V[:, k] = w_last
+        S[np.arange(k), np.arange(k)] = thetas[:k]
+        j0 = k
     return FiedlerResult(theta, y, res, opts.max_restarts, False)
 
 

@@ -47,7 +47,7 @@ int launch_cut(const LevelGraph& G, const Tile* tiles, int ntiles, Unit* units,
 int launch_cc_spread(const LevelGraph& G, const int32_t* parent, const uint64_t* cmin,
                      uint64_t* ckey, int* flag, cudaStream_t s);
 int solver_setup(Unit* units, int nunits, int nd, int krylov, int maxcycles, double tol,
-                 int require_cluster, SolveBufs& B, cudaStream_t s);
+                 int require_cluster, int keep, SolveBufs& B, cudaStream_t s);
 int solver_lanczos(const LevelGraph& G, const Tile* tiles, int ntiles, Unit* units, int nunits,
                    const uint64_t* ckey, SolveBufs& B, int f32, int M, uint64_t sd,
                    const double* from64, const float* from32, int use_graph, cudaStream_t s);
@@ -144,13 +144,15 @@ std::vector<int> prof_capture_end() {
 void prof_replay(const std::vector<int>& pairs) {
   g_prof.pending.insert(g_prof.pending.end(), pairs.begin(), pairs.end());
 }
+int prof_family() { return g_prof.family; }
+
 unsigned long long* prof_bytes(int family) {
   if (g_prof.family == PROF_NONE || family != g_prof.family || !g_prof.dbytes) return nullptr;
   return g_prof.dbytes;
 }
 
 extern "C" void rsb_profile_begin(int family) {
-  g_prof.family = (family >= PROF_LZ_A && family <= PROF_SPMV) ? family : PROF_NONE;
+  g_prof.family = (family >= PROF_LZ_A && family <= PROF_CYCLE) ? family : PROF_NONE;
   g_prof.ms = 0.0;
   g_prof.launches = 0;
   g_prof.pending.clear();
@@ -208,7 +210,7 @@ struct Ctx {
   DevBuf len, slice_sz, scan_tmp, tmp64, newpos;
   DevBuf parent, cmin, ckey, side;
   DevBuf units, tiles, sunits, stiles;
-  DevBuf hist, partials, mom;
+  DevBuf hist, partials, mom, sbuf;
   DevBuf cand[3];
   PrecBufs pb[2];  // 0: FP64, 1: FP32
   DevBuf seg_row0, seg_nleft, seg_child0, seg_p0, seg_split, seg_keystar, seg_unit, seg_ncomp;
@@ -250,6 +252,9 @@ struct Counters {
   int capped;
   long long cycles;
   double resid_max;
+  GridBar gb;
+  int jmin;
+  int pad;
 };
 
 // ----------------------------------------------------------------------------
@@ -309,6 +314,8 @@ extern "C" void rsb_options_default(rsb_options* o) {
   o->use_graph = 1;
   o->validate = 0;
   o->polish_cycles = 0;
+  o->keep = 8;
+  o->tile_rows = 0;
 }
 
 static int check_options(const rsb_options& o) {
@@ -316,6 +323,8 @@ static int check_options(const rsb_options& o) {
   if (o.precision != RSB_FP64 && o.precision != RSB_MIXED)
     return rsb_set_error(RSB_EINVAL, "precision");
   if (o.krylov_dim < 1 || o.krylov_dim > RSB_MAXM) return rsb_set_error(RSB_EINVAL, "krylov_dim");
+  if (o.keep < 0 || o.keep > RSB_MAXKEEP) return rsb_set_error(RSB_EINVAL, "keep");
+  if (o.tile_rows < 0 || o.tile_rows > 64) return rsb_set_error(RSB_EINVAL, "tile_rows");
   if (o.max_restarts < 1) return rsb_set_error(RSB_EINVAL, "max_restarts");
   if (!(o.tol > 0) || !(o.cg_tol > 0) || !(o.mixed_tol > 0))
     return rsb_set_error(RSB_EINVAL, "tolerances");
@@ -410,7 +419,7 @@ static int build_level0(Ctx& c, const std::vector<MeshIn>& meshes, int validate,
 // ----------------------------------------------------------------------------
 // tiles
 // ----------------------------------------------------------------------------
-static void make_tiles(std::vector<Unit>& units, std::vector<Tile>& tiles) {
+static void make_tiles(std::vector<Unit>& units, std::vector<Tile>& tiles, int rmin = RSB_MINR) {
   tiles.clear();
   for (size_t i = 0; i < units.size(); ++i) {
     Unit& u = units[i];
@@ -419,7 +428,7 @@ static void make_tiles(std::vector<Unit>& units, std::vector<Tile>& tiles) {
     // more for large units so that a unit has at most RSB_MAXTILES_PER_UNIT tiles
     int64_t R = (nr + (int64_t)RSB_BLOCK * RSB_MAXTILES_PER_UNIT - 1) /
                 ((int64_t)RSB_BLOCK * RSB_MAXTILES_PER_UNIT);
-    if (R < RSB_MINR) R = RSB_MINR;
+    if (R < rmin) R = rmin;
     const int64_t tr = R * RSB_BLOCK;
     u.tile0 = (int32_t)tiles.size();
     int nt = 0;
@@ -474,6 +483,9 @@ static int reserve_prec(Ctx& c, int f32, int64_t N, int M, SolveBufs& B) {
   B.n_cg = &cn->n_cg;
   B.stat_cycles = &cn->cycles;
   B.h_active = c.h_pinned + 4;
+  B.gb = &cn->gb;
+  B.jmin = &cn->jmin;
+  B.S = dptr<double>(c.sbuf);
   B.partials = dptr<double>(c.partials);
   return RSB_OK;
 }
@@ -511,8 +523,8 @@ static int solve_candidate(Ctx& c, const LevelGraph& G, const Tile* tiles, int n
   // stage 1: working precision
   if ((rc = reserve_prec(c, mixed, G.n, std::max(M, 1), B))) return rc;
   const double tol1 = mixed ? std::max(o.tol, o.mixed_tol) : o.tol;
-  if ((rc = solver_setup(units, nunits, nd, o.krylov_dim, o.max_restarts, tol1, require_cluster, B,
-                         c.s)))
+  if ((rc = solver_setup(units, nunits, nd, o.krylov_dim, o.max_restarts, tol1, require_cluster,
+                         o.keep, B, c.s)))
     return rc;
   RSB_CK(cudaMemsetAsync(&cn->cycles, 0, sizeof(long long), c.s));
   if (inverse) {
@@ -535,7 +547,7 @@ static int solve_candidate(Ctx& c, const LevelGraph& G, const Tile* tiles, int n
     B64.D[0] = B.D[0];
     B64.D[1] = B.D[1];
     if ((rc = solver_setup(units, nunits, nd, o.krylov_dim, o.polish_cycles, o.tol,
-                           require_cluster, B64, c.s)))
+                           require_cluster, o.keep, B64, c.s)))
       return rc;
     if ((rc = solver_lanczos(G, tiles, ntiles, units, nunits, ckey, B64, 0, M, sd, nullptr,
                              (const float*)stage1_vec, use_graph, c.s)))
@@ -548,7 +560,8 @@ static int solve_candidate(Ctx& c, const LevelGraph& G, const Tile* tiles, int n
     if ((rc = reserve_prec(c, 0, G.n, 1, B64))) return rc;
     B64.D[0] = B.D[0];
     B64.D[1] = B.D[1];
-    if ((rc = solver_setup(units, nunits, nd, o.krylov_dim, 1, tol1, require_cluster, B64, c.s)))
+    if ((rc = solver_setup(units, nunits, nd, o.krylov_dim, 1, tol1, require_cluster, o.keep, B64,
+                           c.s)))
       return rc;
     if ((rc = solver_rq_refine(G, tiles, ntiles, units, nunits, ckey, B64,
                                (const float*)stage1_vec, c.s)))
@@ -582,6 +595,7 @@ static int split_units(Ctx& c, const LevelGraph& G, std::vector<Unit>& hunits,
   if ((rc = devbuf_reserve(c.partials, sizeof(double) * (size_t)RSB_MAXC * ntiles + 64))) return rc;
   if ((rc = devbuf_reserve(c.hist, sizeof(int) * 256 * (size_t)nunits))) return rc;
   if ((rc = devbuf_reserve(c.mom, sizeof(double) * 24 * (size_t)nunits))) return rc;
+  if ((rc = devbuf_reserve(c.sbuf, sizeof(double) * RSB_SSTRIDE * (size_t)nunits))) return rc;
   for (int k = 0; k < 3; ++k)
     if ((rc = devbuf_reserve(c.cand[k], sizeof(double) * (size_t)(G.n + 32)))) return rc;
   RSB_CK(cudaMemsetAsync(c.hist.p, 0, sizeof(int) * 256 * (size_t)nunits, c.s));
@@ -789,7 +803,7 @@ static int run_rsb(Ctx& c, const std::vector<MeshIn>& meshes, const std::vector<
       hunits.push_back(u);
     }
     std::vector<Tile> htiles;
-    make_tiles(hunits, htiles);
+    make_tiles(hunits, htiles, o.tile_rows > 0 ? o.tile_rows : RSB_MINR);
     if ((rc = split_units(c, G, hunits, htiles, o, rs))) return rc;
     if (level == 0 && !hunits.empty()) {
       Unit u0;
@@ -1098,11 +1112,12 @@ extern "C" int rsb_fiedler(const rsb_csr* g, const rsb_options* opt, double* lam
   u.k = N / 2;
   u.isn = 1.0 / std::sqrt((double)N);
   std::vector<Tile> htiles;
-  make_tiles(hunits, htiles);
+  make_tiles(hunits, htiles, o.tile_rows > 0 ? o.tile_rows : RSB_MINR);
   const int ntiles = (int)htiles.size();
   if ((rc = devbuf_reserve(c.units, sizeof(Unit))) ||
       (rc = devbuf_reserve(c.tiles, sizeof(Tile) * ntiles)) ||
       (rc = devbuf_reserve(c.partials, sizeof(double) * (size_t)RSB_MAXC * ntiles + 64)) ||
+      (rc = devbuf_reserve(c.sbuf, sizeof(double) * RSB_SSTRIDE)) ||
       (rc = devbuf_reserve(c.cand[0], sizeof(double) * (N + 32))))
     return end_call(c, stream, rc);
   RSB_CK(cudaMemcpyAsync(c.units.p, hunits.data(), sizeof(Unit), cudaMemcpyHostToDevice, c.s));
@@ -1253,7 +1268,7 @@ extern "C" void rsb_release(void) {
                      &c->deg[1], &c->gid[0], &c->gid[1], &c->home[0], &c->home[1],
                      &c->row_seg[0], &c->row_seg[1], &c->len, &c->slice_sz, &c->scan_tmp,
                      &c->tmp64, &c->newpos, &c->parent, &c->cmin, &c->ckey, &c->side, &c->units,
-                     &c->tiles, &c->sunits, &c->stiles, &c->hist, &c->partials, &c->mom,
+                     &c->tiles, &c->sunits, &c->stiles, &c->hist, &c->partials, &c->mom, &c->sbuf,
                      &c->cand[0], &c->cand[1], &c->cand[2], &c->seg_row0, &c->seg_nleft,
                      &c->seg_child0, &c->seg_p0, &c->seg_split, &c->seg_keystar, &c->seg_unit,
                      &c->seg_ncomp, &c->counters, &c->part_concat};

@@ -35,6 +35,8 @@
 #define RSB_MAXM 40                       // Krylov steps per cycle
 #define RSB_MAXD 2                        // deflation vectors (cluster dim 3)
 #define RSB_MAXC (1 + RSB_MAXD + RSB_MAXM)  // Gram-Schmidt coefficients
+#define RSB_MAXKEEP 16                    // Ritz vectors kept by a thick restart
+#define RSB_SSTRIDE (2 * RSB_MAXM * RSB_MAXM)  // doubles of S and Y per unit
 #define RSB_MAXTILES_PER_UNIT 1024
 #define RSB_MINR 2    // minimum rows per thread of a tile
 #define RSB_SUBR 8    // rows per thread handled between two CTA barriers
@@ -65,8 +67,12 @@ struct Unit {
   double isn;            // 1 / sqrt(n)
   double dmax;           // largest weighted degree in the unit
   double tolabs;         // tol * dmax
-  int32_t m;             // Lanczos steps per cycle for this unit
-  int32_t msteps;        // steps available this cycle (m, or fewer on breakdown)
+  int32_t m;             // basis size of a cycle for this unit
+  int32_t msteps;        // basis size reached this cycle (m, or fewer on breakdown)
+  int32_t j0;            // first new step of the cycle (kept Ritz vectors before it)
+  int32_t kk;            // Ritz vectors kept for the next cycle (0: explicit restart)
+  int32_t broke;         // the cycle ended on an invariant subspace
+  int32_t keep;          // thick-restart size requested
   int32_t status;
   int32_t cycles;
   int32_t maxcycles;
@@ -75,7 +81,8 @@ struct Unit {
   int32_t cg_done;
   int64_t inner_total;
   double theta, resid, ynorm2;
-  double beta0;          // norm of the projected start vector
+  double beta0;          // norm of the first new vector of the cycle (unnormalised)
+  double th[RSB_MAXKEEP + 1];  // smallest Ritz values of the last cycle
   double alpha[RSB_MAXM];
   double beta[RSB_MAXM + 1];
   double c1[RSB_MAXC], c2[RSB_MAXC];
@@ -213,24 +220,89 @@ __device__ __forceinline__ bool last_cta(unsigned int* cnt, int ntile) {
   return am_last != 0;
 }
 
+// Grid-wide barrier of a cooperative (co-resident) launch: generation counter,
+// thread 0 of each CTA arrives and waits.  The wait is bounded (about 10 s);
+// on timeout the error word is set and every CTA that reaches a barrier
+// afterwards returns false, so the kernel ends instead of hanging.
+struct GridBar {
+  unsigned int count;
+  unsigned int gen;
+  int err;
+  int pad;
+};
+
+__device__ __forceinline__ bool grid_sync(GridBar* b, unsigned nblocks) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned int* vgen = &b->gen;
+    volatile int* verr = &b->err;
+    const unsigned g = *vgen;
+    __threadfence();
+    const unsigned arrived = atomicAdd(&b->count, 1u);
+    if (arrived == nblocks - 1) {
+      b->count = 0u;
+      __threadfence();
+      atomicAdd(&b->gen, 1u);
+    } else {
+      long long spins = 0;
+      while (*vgen == g) {
+        if (*verr) break;
+        if (++spins > (1ll << 27)) {
+          atomicExch(&b->err, 1);
+          break;
+        }
+        __nanosleep(64);
+      }
+    }
+    __threadfence();
+    s_ok = (*verr == 0);
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+// Loads of data another CTA may have written earlier in the same launch go
+// through L2 (L1 is not coherent across SMs).
+template <bool CO, typename T>
+__device__ __forceinline__ T ldc(const T* p) {
+  if constexpr (CO) return __ldcg(p);
+  else return *p;
+}
+
 // out[c] = sum_t partials[c * stride + t0 + t], t in [0, nt), c in [0, nc);
 // fixed order (lane-strided then butterfly), executed by the whole CTA.
 __device__ __forceinline__ void final_reduce(const double* partials, long long stride, int t0,
                                              int nt, int nc, double* out) {
+  // warp w owns coefficients w, w + 8, ...; every lane issues the loads of all
+  // of its warp's coefficients for 4 tiles before adding, so one batch costs one
+  // round trip to L2 instead of one per coefficient
+  constexpr int CW = (RSB_MAXC + RSB_WARPS - 1) / RSB_WARPS;
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  for (int c = w; c < nc; c += RSB_WARPS) {
-    const double* p = partials + (long long)c * stride + t0;
-    double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
-    int t = lane;
-    for (; t + 96 < nt; t += 128) {
-      s0 += __ldcg(p + t);
-      s1 += __ldcg(p + t + 32);
-      s2 += __ldcg(p + t + 64);
-      s3 += __ldcg(p + t + 96);
+  double acc[CW];
+#pragma unroll
+  for (int i = 0; i < CW; ++i) acc[i] = 0.0;
+  for (int tb = 0; tb < nt; tb += 128) {
+    double v[CW][4];
+#pragma unroll
+    for (int i = 0; i < CW; ++i) {
+      const int c = w + RSB_WARPS * i;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int t = tb + lane + 32 * q;
+        v[i][q] = (c < nc && t < nt) ? __ldcg(partials + (long long)c * stride + t0 + t) : 0.0;
+      }
     }
-    for (; t < nt; t += 32) s0 += __ldcg(p + t);
-    double s = warp_sum((s0 + s1) + (s2 + s3));
-    if (lane == 0) out[c] = s;
+#pragma unroll
+    for (int i = 0; i < CW; ++i) acc[i] += (v[i][0] + v[i][1]) + (v[i][2] + v[i][3]);
+  }
+#pragma unroll
+  for (int i = 0; i < CW; ++i) {
+    const int c = w + RSB_WARPS * i;
+    if (c < nc) {
+      const double s = warp_sum(acc[i]);
+      if (lane == 0) out[c] = s;
+    }
   }
   __syncthreads();
 }
@@ -270,7 +342,11 @@ int rsb_set_error(int code, const std::string& what);
 void rsb_count_launch(int k = 1);
 
 // Kernel timing (rsb_profile_begin/end): families of include/rsb.h.
-enum { PROF_NONE = 0, PROF_LZ_A = 1, PROF_LZ_B = 2, PROF_LZ_C = 3, PROF_CG_AP = 4, PROF_SPMV = 5 };
+enum {
+  PROF_NONE = 0, PROF_LZ_A = 1, PROF_LZ_B = 2, PROF_LZ_C = 3, PROF_CG_AP = 4, PROF_SPMV = 5,
+  PROF_CYCLE = 6
+};
+int prof_family();
 int prof_before(int family, cudaStream_t s);      // event pair index or -1
 void prof_after(int idx, cudaStream_t s);
 void prof_collect();                              // after a stream sync
@@ -346,5 +422,8 @@ struct SolveBufs {
   int* n_cg = nullptr;           // device: units whose CG still runs
   long long* stat_cycles = nullptr;
   int* h_active = nullptr;       // pinned host word for read-backs
+  struct GridBar* gb = nullptr;  // barrier of the persistent cycle kernel
+  double* S = nullptr;           // per-unit projected matrices and Ritz vectors
+  int* jmin = nullptr;           // device: smallest next-cycle start step
   int64_t N = 0;
 };

@@ -53,6 +53,8 @@ struct LzArgs {
   unsigned long long* pb_b;
   unsigned long long* pb_c;
   unsigned long long* pb_cg;
+  double* S;                 // per unit: projected matrix S (M x M) then Ritz vectors Y
+  int* jmin;                 // smallest first step of the next cycle over the units
 };
 
 // CTA-level add of per-thread byte counts to a profiling counter.
@@ -66,10 +68,9 @@ __device__ __forceinline__ int row_width(const int64_t* __restrict__ slice_ptr, 
   return (int)((slice_ptr[(r >> 5) + 1] - slice_ptr[r >> 5]) >> 5);
 }
 
-template <typename V>
+template <typename V, bool CO = false>
 __device__ __forceinline__ V spmv_row(const int64_t* __restrict__ slice_ptr,
-                                      const uint32_t* __restrict__ ent, const V* __restrict__ x,
-                                      int r, V xr) {
+                                      const uint32_t* __restrict__ ent, const V* x, int r, V xr) {
   const int64_t base = slice_ptr[r >> 5];
   const int width = (int)((slice_ptr[(r >> 5) + 1] - base) >> 5);
   const uint32_t* e = ent + base + (r & 31);
@@ -77,7 +78,7 @@ __device__ __forceinline__ V spmv_row(const int64_t* __restrict__ slice_ptr,
 #pragma unroll 4
   for (int k = 0; k < width; ++k) {
     const uint32_t p = __ldg(e + 32 * k);
-    acc += V(ent_w(p)) * (xr - x[ent_col(p)]);
+    acc += V(ent_w(p)) * (xr - ldc<CO>(x + ent_col(p)));
   }
   return acc;
 }
@@ -95,65 +96,86 @@ __device__ __forceinline__ V spmv_row(const int64_t* __restrict__ slice_ptr,
 #define MAXCW ((RSB_MAXC + RSB_WARPS - 1) / RSB_WARPS)
 #define SUBROWS (RSB_BLOCK * RSB_SUBR)
 
-template <typename V, typename B>
-__device__ __forceinline__ void dot_rows(const B* __restrict__ bv, const V* ws, int base, int end,
-                                         Acc<V>& acc) {
-  const int lane = threadIdx.x & 31;
-  int row = base + lane;
-  for (; row + 96 < end; row += 128) {
-    const V b0 = V(bv[row]), b1 = V(bv[row + 32]), b2 = V(bv[row + 64]), b3 = V(bv[row + 96]);
-    const int o = row - base;
-    acc.add(b0 * ws[o]);
-    acc.add(b1 * ws[o + 32]);
-    acc.add(b2 * ws[o + 64]);
-    acc.add(b3 * ws[o + 96]);
-  }
-  for (; row < end; row += 32) acc.add(V(bv[row]) * ws[row - base]);
-}
-
-template <typename V>
-__device__ __forceinline__ void dot_ones(const V* ws, int base, int end, Acc<V>& acc) {
-  const int lane = threadIdx.x & 31;
-  for (int row = base + lane; row < end; row += 32) acc.add(ws[row - base]);
-}
-
-// Warp-per-coefficient dots of basis coefficients [c0, c0 + nc) with the chunk.
+// Warp-per-coefficient dots of basis coefficients [c0, c0 + nc) with the chunk:
+// warp w owns coefficients w, w + 8, ...; each lane walks rows in groups of 4
+// and issues the loads of all of its warp's coefficients for the group before
+// accumulating, so up to 4 * MAXCW loads are in flight per lane.
 template <typename V>
 __device__ __forceinline__ void tile_dots(const LzArgs<V>& a, int nd, int c0, int nc, int base,
                                           int end, const V* ws, Acc<V> (&acc)[MAXCW]) {
-  const int w = threadIdx.x >> 5;
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const V* qp[MAXCW];
+  const double* dp[MAXCW];
+  int kind[MAXCW];  // -1 none, 0 ones (u0), 1 FP64 deflation vector, 2 basis vector
 #pragma unroll
   for (int i = 0; i < MAXCW; ++i) {
     const int c = w + RSB_WARPS * i;
-    if (c < nc) {
-      const int cc = c0 + c;
-      if (cc == 0) dot_ones<V>(ws, base, end, acc[i]);
-      else if (cc <= nd) dot_rows<V, double>(cc == 1 ? a.D0 : a.D1, ws, base, end, acc[i]);
-      else dot_rows<V, V>(a.Q + (long long)(cc - 1 - nd) * a.N, ws, base, end, acc[i]);
+    const int cc = c0 + c;
+    qp[i] = nullptr;
+    dp[i] = nullptr;
+    if (c >= nc) kind[i] = -1;
+    else if (cc == 0) kind[i] = 0;
+    else if (cc <= nd) {
+      kind[i] = 1;
+      dp[i] = cc == 1 ? a.D0 : a.D1;
+    } else {
+      kind[i] = 2;
+      qp[i] = a.Q + (long long)(cc - 1 - nd) * a.N;
     }
+  }
+  if (kind[0] < 0) return;
+  for (int row = base + lane; row < end; row += 128) {
+    V wv[4];
+    bool ok[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      ok[q] = row + 32 * q < end;
+      wv[q] = ok[q] ? ws[row + 32 * q - base] : V(0);
+    }
+    V b[MAXCW][4];
+#pragma unroll
+    for (int i = 0; i < MAXCW; ++i)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int r = row + 32 * q;
+        b[i][q] = V(0);
+        if (ok[q]) {
+          if (kind[i] == 2) b[i][q] = qp[i][r];
+          else if (kind[i] == 1) b[i][q] = V(dp[i][r]);
+          else if (kind[i] == 0) b[i][q] = V(1);
+        }
+      }
+#pragma unroll
+    for (int i = 0; i < MAXCW; ++i)
+      if (kind[i] >= 0) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+          if (ok[q]) acc[i].add(b[i][q] * wv[q]);
+      }
   }
 }
 
 template <typename V>
-__device__ __forceinline__ void store_dots(const LzArgs<V>& a, int nc, Acc<V> (&acc)[MAXCW]) {
+__device__ __forceinline__ void store_dots(const LzArgs<V>& a, int nc, Acc<V> (&acc)[MAXCW],
+                                           int tix) {
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
 #pragma unroll
   for (int i = 0; i < MAXCW; ++i) {
     const int c = w + RSB_WARPS * i;
     if (c < nc) {
       const double s = warp_sum(acc[i].get());
-      if (lane == 0) a.partials[(long long)c * a.stride + blockIdx.x] = s;
+      if (lane == 0) a.partials[(long long)c * a.stride + tix] = s;
     }
   }
 }
 
 // w[rr] -= sum_c coef[c] basis_c for the RSB_SUBR rows of this thread
 // (rows base + rr*RSB_BLOCK + tid), coefficient-outer.
-template <typename V>
+template <typename V, bool CO>
 __device__ __forceinline__ void gs_update_rows(const LzArgs<V>& a, const Unit& u,
                                                const double* coef, int nd, int nq, int base,
                                                int end, V (&w)[RSB_SUBR]) {
-  const V c0 = V(coef[0] * u.isn);
+  const V c0 = V(ldc<CO>(coef) * u.isn);
 #pragma unroll
   for (int rr = 0; rr < RSB_SUBR; ++rr) {
     const int r = base + rr * RSB_BLOCK + threadIdx.x;
@@ -161,7 +183,7 @@ __device__ __forceinline__ void gs_update_rows(const LzArgs<V>& a, const Unit& u
   }
   for (int l = 0; l < nd; ++l) {
     const double* d = l == 0 ? a.D0 : a.D1;
-    const V cl = V(coef[1 + l]);
+    const V cl = V(ldc<CO>(coef + 1 + l));
 #pragma unroll
     for (int rr = 0; rr < RSB_SUBR; ++rr) {
       const int r = base + rr * RSB_BLOCK + threadIdx.x;
@@ -169,41 +191,59 @@ __device__ __forceinline__ void gs_update_rows(const LzArgs<V>& a, const Unit& u
     }
   }
   const double* cq = coef + 1 + nd;
-  for (int k = 0; k < nq; ++k) {
-    const V ck = V(cq[k]);
-    const V* q = a.Q + (long long)k * a.N;
-    V qv[RSB_SUBR];
+  bool ok[RSB_SUBR];
 #pragma unroll
-    for (int rr = 0; rr < RSB_SUBR; ++rr) {
-      const int r = base + rr * RSB_BLOCK + threadIdx.x;
-      qv[rr] = r < end ? q[r] : V(0);
+  for (int rr = 0; rr < RSB_SUBR; ++rr) ok[rr] = base + rr * RSB_BLOCK + (int)threadIdx.x < end;
+  int k = 0;
+  for (; k + 4 <= nq; k += 4) {  // four basis vectors per round: 4 * RSB_SUBR loads in flight
+    V qv[4][RSB_SUBR];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const V* q = a.Q + (long long)(k + i) * a.N + base + threadIdx.x;
+#pragma unroll
+      for (int rr = 0; rr < RSB_SUBR; ++rr) qv[i][rr] = ok[rr] ? q[rr * RSB_BLOCK] : V(0);
     }
 #pragma unroll
-    for (int rr = 0; rr < RSB_SUBR; ++rr) w[rr] -= ck * qv[rr];
+    for (int i = 0; i < 4; ++i) {
+      const V ck = V(ldc<CO>(cq + k + i));
+#pragma unroll
+      for (int rr = 0; rr < RSB_SUBR; ++rr) w[rr] -= ck * qv[i][rr];
+    }
+  }
+  for (; k < nq; ++k) {
+    const V ck = V(ldc<CO>(cq + k));
+    const V* q = a.Q + (long long)k * a.N + base + threadIdx.x;
+#pragma unroll
+    for (int rr = 0; rr < RSB_SUBR; ++rr)
+      if (ok[rr]) w[rr] -= ck * q[rr * RSB_BLOCK];
   }
 }
 
 // ----------------------------------------------------------------------------
-// Lanczos step kernels
+// Lanczos step (thick-restarted, full re-orthogonalisation): per-tile bodies
+// (CO = running inside the persistent cycle kernel, where data written by
+// other CTAs earlier in the launch is read through L2) and the stand-alone
+// kernels that wrap them.
+//   A(j): q_j = src / beta (src is the unnormalised new vector), w = L q_j,
+//         first Gram-Schmidt pass coefficients c1 = [1, D, q_0..q_j]^T w;
+//   B(j): w -= basis c1, second-pass coefficients c2; column j of the
+//         projected matrix S = Q^T L Q is c1 + c2 on q_0..q_j;
+//   C(j): w -= basis c2, beta_{j+1} = ||w|| (w stays unnormalised for A(j+1)).
 // ----------------------------------------------------------------------------
-template <typename V>
-__global__ void __launch_bounds__(RSB_BLOCK) k_lz_a(LzArgs<V> a, int j) {
-  __shared__ V ws[SUBROWS];
-  __shared__ double out[RSB_MAXC];
-  const Tile t = a.tiles[blockIdx.x];
+__device__ __forceinline__ double* unit_S(double* S, int ui) { return S + (long long)ui * RSB_SSTRIDE; }
+
+template <typename V, bool CO>
+__device__ __forceinline__ void lz_a_t(const LzArgs<V>& a, int j, int tix, V* ws, double* out) {
+  const Tile t = a.tiles[tix];
   Unit& u = a.units[t.unit];
-  if (u.status != U_ACTIVE || j >= u.msteps) return;
+  if (ldc<CO>(&u.status) != U_ACTIVE || j >= ldc<CO>(&u.msteps) || j < ldc<CO>(&u.j0)) return;
   const V* src = (j & 1) ? a.W1 : a.W0;
   V* dst = (j & 1) ? a.W0 : a.W1;
   V* qj = a.Q + (long long)j * a.N;
-  const V* qjm = j ? a.Q + (long long)(j - 1) * a.N : nullptr;
-  const double sc = 1.0 / (j == 0 ? u.beta0 : u.beta[j]);
+  const double sc = 1.0 / (j == ldc<CO>(&u.j0) ? ldc<CO>(&u.beta0) : ldc<CO>(&u.beta[j]));
   const V s = V(sc);
-  const V bj = V(j ? u.beta[j] : 0.0);
-  const bool last = (j == u.m - 1);
   const int nd = u.nd;
-  const int nc = last ? 1 : (2 + nd + j);
-  const int c0 = last ? (1 + nd + j) : 0;
+  const int nc = 2 + nd + j;
   Acc<V> acc[MAXCW];
   unsigned long long pbytes = 0;
   for (int base = t.row0; base < t.row1; base += SUBROWS) {
@@ -214,44 +254,35 @@ __global__ void __launch_bounds__(RSB_BLOCK) k_lz_a(LzArgs<V> a, int j) {
       V w = V(0);
       if (r < end) {
         const V xr = src[r];
-        w = s * spmv_row<V>(a.slice_ptr, a.ent, src, r, xr);
-        if (j) w -= bj * qjm[r];
+        w = s * spmv_row<V, CO>(a.slice_ptr, a.ent, src, r, xr);
         qj[r] = s * xr;
-        if (!last) dst[r] = w;
+        dst[r] = w;
         if (a.pb_a)
           pbytes += 4ull * row_width(a.slice_ptr, r) +
-                    sizeof(V) * (unsigned long long)(2 + (j > 0) + !last + (last ? 1 : j + 1)) +
-                    (last ? 0ull : 8ull * nd);
+                    sizeof(V) * (unsigned long long)(4 + j) + 8ull * nd;
       }
       ws[rr * RSB_BLOCK + threadIdx.x] = w;
     }
     __syncthreads();
-    tile_dots<V>(a, nd, c0, nc, base, end, ws, acc);
+    tile_dots<V>(a, nd, 0, nc, base, end, ws, acc);
     __syncthreads();
   }
-  store_dots<V>(a, nc, acc);
+  store_dots<V>(a, nc, acc, tix);
   if (a.pb_a) prof_add(a.pb_a, pbytes);
   if (last_cta(&u.cnt, u.ntile)) {
     final_reduce(a.partials, a.stride, u.tile0, u.ntile, nc, out);
     if (threadIdx.x == 0) {
-      if (last) {
-        u.alpha[j] = out[0];
-      } else {
-        u.c1[0] = out[0] * u.isn;
-        for (int c = 1; c < nc; ++c) u.c1[c] = out[c];
-        u.alpha[j] = out[nc - 1];
-      }
+      u.c1[0] = out[0] * u.isn;
+      for (int c = 1; c < nc; ++c) u.c1[c] = out[c];
     }
   }
 }
 
-template <typename V>
-__global__ void __launch_bounds__(RSB_BLOCK) k_lz_b(LzArgs<V> a, int j) {
-  __shared__ V ws[SUBROWS];
-  __shared__ double out[RSB_MAXC];
-  const Tile t = a.tiles[blockIdx.x];
+template <typename V, bool CO>
+__device__ __forceinline__ void lz_b_t(const LzArgs<V>& a, int j, int tix, V* ws, double* out) {
+  const Tile t = a.tiles[tix];
   Unit& u = a.units[t.unit];
-  if (u.status != U_ACTIVE || j >= u.msteps || j == u.m - 1) return;
+  if (ldc<CO>(&u.status) != U_ACTIVE || j >= ldc<CO>(&u.msteps) || j < ldc<CO>(&u.j0)) return;
   V* w_ = (j & 1) ? a.W0 : a.W1;
   const int nd = u.nd;
   const int nc = 2 + nd + j;
@@ -265,7 +296,7 @@ __global__ void __launch_bounds__(RSB_BLOCK) k_lz_b(LzArgs<V> a, int j) {
       const int r = base + rr * RSB_BLOCK + threadIdx.x;
       w[rr] = r < end ? w_[r] : V(0);
     }
-    gs_update_rows<V>(a, u, u.c1, nd, j + 1, base, end, w);
+    gs_update_rows<V, CO>(a, u, u.c1, nd, j + 1, base, end, w);
 #pragma unroll
     for (int rr = 0; rr < RSB_SUBR; ++rr) {
       const int r = base + rr * RSB_BLOCK + threadIdx.x;
@@ -279,7 +310,7 @@ __global__ void __launch_bounds__(RSB_BLOCK) k_lz_b(LzArgs<V> a, int j) {
     tile_dots<V>(a, nd, 0, nc, base, end, ws, acc);
     __syncthreads();
   }
-  store_dots<V>(a, nc, acc);
+  store_dots<V>(a, nc, acc, tix);
   if (a.pb_b) prof_add(a.pb_b, pbytes);
   if (last_cta(&u.cnt, u.ntile)) {
     final_reduce(a.partials, a.stride, u.tile0, u.ntile, nc, out);
@@ -287,16 +318,22 @@ __global__ void __launch_bounds__(RSB_BLOCK) k_lz_b(LzArgs<V> a, int j) {
       u.c2[0] = out[0] * u.isn;
       for (int c = 1; c < nc; ++c) u.c2[c] = out[c];
     }
+    __syncthreads();
+    double* Sm = unit_S(a.S, t.unit);
+    for (int k = threadIdx.x; k <= j; k += RSB_BLOCK) {
+      const double v = ldc<CO>(&u.c1[1 + nd + k]) + out[1 + nd + k];
+      Sm[k * RSB_MAXM + j] = v;
+      Sm[j * RSB_MAXM + k] = v;
+    }
   }
 }
 
-template <typename V>
-__global__ void __launch_bounds__(RSB_BLOCK) k_lz_c(LzArgs<V> a, int j, double breakdown) {
-  __shared__ double sm[RSB_WARPS];
-  __shared__ double out[1];
-  const Tile t = a.tiles[blockIdx.x];
+template <typename V, bool CO>
+__device__ __forceinline__ void lz_c_t(const LzArgs<V>& a, int j, double breakdown, int tix,
+                                       double* sm, double* out) {
+  const Tile t = a.tiles[tix];
   Unit& u = a.units[t.unit];
-  if (u.status != U_ACTIVE || j >= u.msteps || j == u.m - 1) return;
+  if (ldc<CO>(&u.status) != U_ACTIVE || j >= ldc<CO>(&u.msteps) || j < ldc<CO>(&u.j0)) return;
   V* w_ = (j & 1) ? a.W0 : a.W1;
   const int nd = u.nd;
   Acc<V> acc;
@@ -309,7 +346,7 @@ __global__ void __launch_bounds__(RSB_BLOCK) k_lz_c(LzArgs<V> a, int j, double b
       const int r = base + rr * RSB_BLOCK + threadIdx.x;
       w[rr] = r < end ? w_[r] : V(0);
     }
-    gs_update_rows<V>(a, u, u.c2, nd, j + 1, base, end, w);
+    gs_update_rows<V, CO>(a, u, u.c2, nd, j + 1, base, end, w);
 #pragma unroll
     for (int rr = 0; rr < RSB_SUBR; ++rr) {
       const int r = base + rr * RSB_BLOCK + threadIdx.x;
@@ -322,204 +359,223 @@ __global__ void __launch_bounds__(RSB_BLOCK) k_lz_c(LzArgs<V> a, int j, double b
   }
   if (a.pb_c) prof_add(a.pb_c, pbytes);
   const double sum = block_sum(acc.get(), sm);
-  if (threadIdx.x == 0) a.partials[blockIdx.x] = sum;
+  if (threadIdx.x == 0) a.partials[tix] = sum;
   if (last_cta(&u.cnt, u.ntile)) {
     final_reduce(a.partials, a.stride, u.tile0, u.ntile, 1, out);
     if (threadIdx.x == 0) {
       const double b = sqrt(out[0]);
-      if (b <= breakdown * u.dmax) u.msteps = j + 1;  // invariant subspace: cycle ends
-      else u.beta[j + 1] = b;
+      u.beta[j + 1] = b;
+      if (b <= breakdown * u.dmax) {  // invariant subspace: the cycle ends here
+        u.msteps = j + 1;
+        u.broke = 1;
+      }
     }
   }
 }
 
-// ----------------------------------------------------------------------------
-// smallest eigenpair of the symmetric tridiagonal T_K (one warp per unit)
-// ----------------------------------------------------------------------------
-// Eigenvalue: Sturm-count multisection (32 shifts per round, one per lane).
-// The count of eigenvalues below sigma is the number of sign changes of the
-// leading principal minors p_k = det(T_k - sigma I), p_k = (alpha_k - sigma)
-// p_{k-1} - beta_k^2 p_{k-2} (a zero takes the sign opposite to its
-// predecessor); two FMAs per step and exact power-of-two rescaling, no
-// division.  Eigenvector: inverse iteration on T - theta I, factorised once by
-// Gaussian elimination with partial pivoting (reciprocals from an FP32 seed
-// refined by two Newton steps to FP64 accuracy), then two multiply-only solves.
-__device__ __forceinline__ double fast_rcp(double x) {
-  const double ax = fabs(x);
-  if (!(ax > 1e-30 && ax < 1e30)) return 1.0 / x;
-  double r = (double)__frcp_rn((float)x);
-  r = r * fma(-x, r, 2.0);
-  r = r * fma(-x, r, 2.0);
-  return r;
+template <typename V>
+__global__ void __launch_bounds__(RSB_BLOCK, 2) k_lz_a(LzArgs<V> a, int j) {
+  __shared__ V ws[SUBROWS];
+  __shared__ double out[RSB_MAXC];
+  lz_a_t<V, false>(a, j, blockIdx.x, ws, out);
 }
 
-__device__ int sturm_count(const double* al, const double* b2, int K, double sig) {
-  const double BIG = 0x1p500, SMALL = 0x1p-500;
-  double pm = 1.0;
-  double p = al[0] - sig;
-  int sprev = 1, cnt = 0;
-  int sg = p > 0.0 ? 1 : (p < 0.0 ? -1 : -sprev);
-  cnt += sg != sprev;
-  sprev = sg;
-  for (int k = 1; k < K; ++k) {
-    const double pn = fma(al[k] - sig, p, -b2[k] * pm);
-    pm = p;
-    p = pn;
-    const double ap = fabs(p);
-    if (ap > BIG) {
-      p *= SMALL;
-      pm *= SMALL;
-    } else if (ap < SMALL && ap > 0.0) {
-      p *= BIG;
-      pm *= BIG;
-    }
-    sg = p > 0.0 ? 1 : (p < 0.0 ? -1 : -sprev);
-    cnt += sg != sprev;
-    sprev = sg;
-  }
-  return cnt;
+template <typename V>
+__global__ void __launch_bounds__(RSB_BLOCK, 2) k_lz_b(LzArgs<V> a, int j) {
+  __shared__ V ws[SUBROWS];
+  __shared__ double out[RSB_MAXC];
+  lz_b_t<V, false>(a, j, blockIdx.x, ws, out);
 }
 
-struct TriLU {
-  double d[RSB_MAXM], du[RSB_MAXM], du2[RSB_MAXM], f[RSB_MAXM], rd[RSB_MAXM];
-  unsigned char swp[RSB_MAXM];
+template <typename V>
+__global__ void __launch_bounds__(RSB_BLOCK) k_lz_c(LzArgs<V> a, int j, double breakdown) {
+  __shared__ double sm[RSB_WARPS];
+  __shared__ double out[1];
+  lz_c_t<V, false>(a, j, breakdown, blockIdx.x, sm, out);
+}
+
+// ----------------------------------------------------------------------------
+// Ritz pairs of S (K x K, K <= 40): parallel cyclic Jacobi in one CTA (FP64).
+// Rounds of the round-robin ("circle") ordering rotate K/2 disjoint pairs at
+// once; each rotation is the symmetric 2x2 Schur rotation (Golub & Van Loan
+// §8.5).  Output: theta_0..theta_kk (ascending) and their eigenvectors as the
+// Y columns of the unit's storage.
+// ----------------------------------------------------------------------------
+template <typename T>
+struct JacShared {
+  T A[RSB_MAXM][RSB_MAXM + 1];
+  T Z[RSB_MAXM][RSB_MAXM + 1];
+  T c[RSB_MAXM / 2], s[RSB_MAXM / 2];
+  int p[RSB_MAXM / 2], q[RSB_MAXM / 2];
+  double red[RSB_WARPS];
+  int rank[RSB_MAXM];
 };
 
-__device__ void tri_factor(const double* al, const double* be, int K, double theta, double pert,
-                           TriLU& F) {
-  double dl[RSB_MAXM];
-  for (int k = 0; k < K; ++k) {
-    F.d[k] = al[k] - theta;
-    F.du[k] = (k + 1 < K) ? be[k + 1] : 0.0;
-    dl[k] = (k + 1 < K) ? be[k + 1] : 0.0;
-    F.du2[k] = 0.0;
-    F.swp[k] = 0;
+// T = double for the FP64 path; T = float for the mixed path, whose Lanczos
+// vectors are FP32 (so FP32-accurate Ritz vectors lose nothing) and whose
+// eigenvalue comes from the FP64 Rayleigh quotient at the end.
+template <typename T, bool CO>
+__device__ void lz_eig_u(Unit& u, double* Sm, JacShared<T>& J) {
+  if (ldc<CO>(&u.status) != U_ACTIVE) return;
+  const int tid = threadIdx.x;
+  const int K = ldc<CO>(&u.msteps);
+  const int n2 = K + (K & 1);
+  for (int idx = tid; idx < n2 * n2; idx += RSB_BLOCK) {
+    const int i = idx / n2, k = idx % n2;
+    J.A[i][k] = (i < K && k < K) ? T(ldc<CO>(Sm + i * RSB_MAXM + k)) : T(0);
+    J.Z[i][k] = i == k ? T(1) : T(0);
   }
-  for (int k = 0; k + 1 < K; ++k) {
-    if (fabs(F.d[k]) >= fabs(dl[k])) {
-      if (F.d[k] == 0.0) F.d[k] = pert;
-      const double fk = dl[k] * fast_rcp(F.d[k]);
-      F.f[k] = fk;
-      F.d[k + 1] -= fk * F.du[k];
-    } else {
-      const double fk = F.d[k] * fast_rcp(dl[k]);
-      F.f[k] = fk;
-      F.swp[k] = 1;
-      F.d[k] = dl[k];
-      const double tmp = F.d[k + 1];
-      F.d[k + 1] = F.du[k] - fk * tmp;
-      if (k + 2 < K) {
-        F.du2[k] = F.du[k + 1];
-        F.du[k + 1] = -fk * F.du2[k];
+  __syncthreads();
+  double fro = 0.0;
+  for (int idx = tid; idx < K * K; idx += RSB_BLOCK) {
+    const double x = (double)J.A[idx / K][idx % K];
+    fro += x * x;
+  }
+  fro = block_sum(fro, J.red);
+  if (tid == 0) J.red[0] = fro;
+  __syncthreads();
+  fro = J.red[0];
+  __syncthreads();
+  const double eps2 = sizeof(T) == 8 ? 1e-30 : 1e-14;
+  const double thr = fro * eps2;
+  for (int sweep = 0; sweep < 20; ++sweep) {
+    double off = 0.0;
+    for (int idx = tid; idx < K * K; idx += RSB_BLOCK) {
+      const int i = idx / K, k = idx % K;
+      if (i < k) off += (double)J.A[i][k] * (double)J.A[i][k];
+    }
+    off = block_sum(off, J.red);
+    if (tid == 0) J.red[0] = off;
+    __syncthreads();
+    off = J.red[0];
+    __syncthreads();
+    if (off <= thr) break;
+    for (int rnd = 0; rnd < n2 - 1; ++rnd) {
+      if (tid < n2 / 2) {
+        int pa = tid == 0 ? 0 : ((tid + rnd - 1) % (n2 - 1)) + 1;
+        int pb = ((n2 - 1 - tid + rnd - 1) % (n2 - 1)) + 1;
+        if (pa > pb) { const int tt = pa; pa = pb; pb = tt; }
+        T cc = T(1), ss = T(0);
+        const T apq = J.A[pa][pb];
+        if (pb < K && apq != T(0)) {
+          const T tau = (J.A[pb][pb] - J.A[pa][pa]) / (T(2) * apq);
+          const T tt = tau >= T(0) ? T(1) / (tau + sqrt(T(1) + tau * tau))
+                                   : T(-1) / (-tau + sqrt(T(1) + tau * tau));
+          cc = T(1) / sqrt(T(1) + tt * tt);
+          ss = tt * cc;
+        }
+        J.p[tid] = pa;
+        J.q[tid] = pb;
+        J.c[tid] = cc;
+        J.s[tid] = ss;
       }
-      F.du[k] = tmp;
+      __syncthreads();
+      for (int task = tid; task < (n2 / 2) * n2; task += RSB_BLOCK) {
+        const int i = task / n2, r = task % n2;
+        const int pa = J.p[i], pb = J.q[i];
+        const T cc = J.c[i], ss = J.s[i];
+        const T x = J.A[r][pa], y = J.A[r][pb];
+        J.A[r][pa] = cc * x - ss * y;
+        J.A[r][pb] = ss * x + cc * y;
+        const T zx = J.Z[r][pa], zy = J.Z[r][pb];
+        J.Z[r][pa] = cc * zx - ss * zy;
+        J.Z[r][pb] = ss * zx + cc * zy;
+      }
+      __syncthreads();
+      for (int task = tid; task < (n2 / 2) * n2; task += RSB_BLOCK) {
+        const int i = task / n2, col = task % n2;
+        const int pa = J.p[i], pb = J.q[i];
+        const T cc = J.c[i], ss = J.s[i];
+        const T x = J.A[pa][col], y = J.A[pb][col];
+        J.A[pa][col] = cc * x - ss * y;
+        J.A[pb][col] = ss * x + cc * y;
+      }
+      __syncthreads();
     }
   }
-  if (F.d[K - 1] == 0.0) F.d[K - 1] = pert;
-  for (int k = 0; k < K; ++k) F.rd[k] = fast_rcp(F.d[k]);
+  // ascending order (ties by index)
+  if (tid < K) {
+    const T e = J.A[tid][tid];
+    int rk = 0;
+    for (int l = 0; l < K; ++l) {
+      const T f = J.A[l][l];
+      rk += (f < e) || (f == e && l < tid);
+    }
+    J.rank[tid] = rk;
+  }
+  __syncthreads();
+  const int kk = ldc<CO>(&u.broke) ? 0 : min(u.keep, K - 1);
+  double* Ym = Sm + RSB_MAXM * RSB_MAXM;
+  for (int idx = tid; idx < K * K; idx += RSB_BLOCK) {
+    const int l = idx / K, i = idx % K;  // eigenvector i (unsorted), component l
+    const int rk = J.rank[i];
+    if (rk <= kk) Ym[l * RSB_MAXM + rk] = (double)J.Z[l][i];
+  }
+  if (tid < K) {
+    const int rk = J.rank[tid];
+    if (rk <= kk) u.th[rk] = (double)J.A[tid][tid];
+    if (rk == 0) u.theta = (double)J.A[tid][tid];
+  }
+  if (tid == 0) u.kk = kk;
+  __syncthreads();
 }
 
-__device__ void tri_solve(const TriLU& F, int K, double* x) {
-  for (int k = 0; k + 1 < K; ++k) {
-    if (F.swp[k]) {
-      const double tb = x[k];
-      x[k] = x[k + 1];
-      x[k + 1] = tb - F.f[k] * x[k + 1];
-    } else {
-      x[k + 1] -= F.f[k] * x[k];
-    }
-  }
-  x[K - 1] *= F.rd[K - 1];
-  if (K >= 2) x[K - 2] = (x[K - 2] - F.du[K - 2] * x[K - 1]) * F.rd[K - 2];
-  for (int k = K - 3; k >= 0; --k)
-    x[k] = (x[k] - F.du[k] * x[k + 1] - F.du2[k] * x[k + 2]) * F.rd[k];
-}
-
-__global__ void k_lz_tridiag(Unit* units, int nunits) {
-  const int ui = blockIdx.x;
-  if (ui >= nunits) return;
-  Unit& u = units[ui];
-  if (u.status != U_ACTIVE) return;
-  const int lane = threadIdx.x;
-  const int K = u.msteps;
-  double al[RSB_MAXM], b2[RSB_MAXM];
-  double lo = 1e300, hi = -1e300;
-  for (int k = 0; k < K; ++k) {
-    al[k] = u.alpha[k];
-    b2[k] = k > 0 ? u.beta[k] * u.beta[k] : 0.0;
-    const double r = (k > 0 ? fabs(u.beta[k]) : 0.0) + (k + 1 < K ? fabs(u.beta[k + 1]) : 0.0);
-    lo = fmin(lo, al[k] - r);
-    hi = fmax(hi, al[k] + r);
-  }
-  const double tnorm = fmax(fabs(lo), fabs(hi));
-  // multisection for the smallest eigenvalue: count(lo) = 0 <= count(hi)
-  for (int it = 0; it < 40; ++it) {
-    if (hi - lo <= 2.0 * DBL_EPSILON * fmax(fabs(lo), fabs(hi)) + DBL_MIN) break;
-    const double step = (hi - lo) * (1.0 / 33.0);
-    const double sig = lo + step * (lane + 1);
-    const int c = sturm_count(al, b2, K, sig);
-    const unsigned m = __ballot_sync(0xffffffffu, c >= 1);
-    const int first = m ? __ffs(m) - 1 : 32;
-    const double nhi = first < 32 ? lo + step * (first + 1) : hi;
-    const double nlo = first > 0 ? lo + step * first : lo;
-    lo = nlo;
-    hi = nhi;
-  }
-  const double theta = 0.5 * (lo + hi);
-  if (lane == 0) {
-    TriLU F;
-    const double pert = DBL_EPSILON * fmax(tnorm, DBL_MIN);
-    tri_factor(al, u.beta, K, theta, pert, F);
-    double x[RSB_MAXM];
-    for (int k = 0; k < K; ++k) x[k] = 1.0;
-    for (int it = 0; it < 2; ++it) {
-      tri_solve(F, K, x);
-      double nrm = 0.0;
-      for (int k = 0; k < K; ++k) nrm = fma(x[k], x[k], nrm);
-      nrm = 1.0 / sqrt(nrm);
-      for (int k = 0; k < K; ++k) x[k] *= nrm;
-    }
-    for (int k = 0; k < K; ++k) u.t[k] = x[k];
-    u.theta = theta;
-  }
+template <typename T>
+__global__ void __launch_bounds__(RSB_BLOCK) k_lz_eig(Unit* units, double* S, int nunits) {
+  __shared__ JacShared<T> J;
+  if ((int)blockIdx.x >= nunits) return;
+  lz_eig_u<T, false>(units[blockIdx.x], unit_S(S, blockIdx.x), J);
 }
 
 // ----------------------------------------------------------------------------
-// Ritz vector, residual, restart
+// Ritz vector and thick-restart basis (per row, in place): y = Q s_0 into Y;
+// q_i <- Q s_i for i < kk; the residual direction moves to W[kk & 1] so that
+// the next cycle's first step reads it.
 // ----------------------------------------------------------------------------
-template <typename V>
-__global__ void __launch_bounds__(RSB_BLOCK) k_lz_ritz(LzArgs<V> a) {
-  const Tile t = a.tiles[blockIdx.x];
+template <typename V, bool CO>
+__device__ __forceinline__ void lz_ritz_t(const LzArgs<V>& a, int tix) {
+  const Tile t = a.tiles[tix];
   const Unit& u = a.units[t.unit];
-  if (u.status != U_ACTIVE) return;
-  const int K = u.msteps;
+  if (ldc<CO>(&u.status) != U_ACTIVE) return;
+  const int K = ldc<CO>(&u.msteps);
+  const int kk = ldc<CO>(&u.kk);
+  const double* Ym = unit_S(a.S, t.unit) + RSB_MAXM * RSB_MAXM;
+  const V* wl = (K & 1) ? a.W1 : a.W0;
+  V* wn = (kk & 1) ? a.W1 : a.W0;
   for (int r = t.row0 + threadIdx.x; r < t.row1; r += RSB_BLOCK) {
-    V y = V(0);
-    const V* q = a.Q + r;
-#pragma unroll 4
-    for (int k = 0; k < K; ++k) y += V(u.t[k]) * q[(long long)k * a.N];
-    a.Y[r] = y;
+    V q[RSB_MAXM];
+#pragma unroll
+    for (int l = 0; l < RSB_MAXM; ++l) q[l] = l < K ? a.Q[(long long)l * a.N + r] : V(0);
+    for (int i = 0; i <= kk; ++i) {
+      V acc = V(0);
+#pragma unroll
+      for (int l = 0; l < RSB_MAXM; ++l)
+        if (l < K) acc += V(ldc<CO>(Ym + l * RSB_MAXM + i)) * q[l];
+      if (i == 0) a.Y[r] = acc;
+      if (i < kk) a.Q[(long long)i * a.N + r] = acc;
+    }
+    if (kk > 0 && wn != wl) wn[r] = wl[r];
   }
+  if (CO && a.pb_a && threadIdx.x == 0)
+    atomicAdd(a.pb_a, (unsigned long long)(t.row1 - t.row0) * sizeof(V) * (K + kk + 1));
 }
 
-// Residual of y (src) with theta, plus the projection dots of y against the
-// fixed basis.  mode 0: Lanczos cycle end (decides convergence); mode 1: the
-// start vector only (no residual).
-template <typename V>
-__global__ void __launch_bounds__(RSB_BLOCK) k_lz_resid(LzArgs<V> a, const V* __restrict__ y,
-                                                        int mode) {
-  __shared__ double sm[RSB_WARPS];
-  __shared__ double out[3 + RSB_MAXD];
-  const Tile t = a.tiles[blockIdx.x];
+// Residual of y with theta, plus the projection dots of y against the fixed
+// basis.  mode 0: Lanczos cycle end (decides convergence); mode 1: the start
+// vector only (no residual).
+template <typename V, bool CO>
+__device__ __forceinline__ void lz_resid_t(const LzArgs<V>& a, const V* y, int mode, int tix,
+                                           double* sm, double* out) {
+  const Tile t = a.tiles[tix];
   Unit& u = a.units[t.unit];
-  if (u.status != U_ACTIVE) return;
+  if (ldc<CO>(&u.status) != U_ACTIVE) return;
   const int nd = u.nd;
-  const V th = V(u.theta);
+  const V th = V(ldc<CO>(&u.theta));
   Acc<V> r2, y2, ys, d0, d1;
   for (int r = t.row0 + threadIdx.x; r < t.row1; r += RSB_BLOCK) {
     const V yr = y[r];
     if (mode == 0) {
-      const V res = spmv_row<V>(a.slice_ptr, a.ent, y, r, yr) - th * yr;
+      const V res = spmv_row<V, CO>(a.slice_ptr, a.ent, y, r, yr) - th * yr;
       r2.add(res * res);
     }
     y2.add(yr * yr);
@@ -527,11 +583,17 @@ __global__ void __launch_bounds__(RSB_BLOCK) k_lz_resid(LzArgs<V> a, const V* __
     if (nd > 0) d0.add(V(a.D0[r]) * yr);
     if (nd > 1) d1.add(V(a.D1[r]) * yr);
   }
+  if (CO && a.pb_a && threadIdx.x == 0) {
+    unsigned long long b = 0;
+    for (int r = t.row0; r < t.row1; ++r) b += 4ull * row_width(a.slice_ptr, r);
+    b += (unsigned long long)(t.row1 - t.row0) * (sizeof(V) + 8ull * nd);
+    atomicAdd(a.pb_a, b);
+  }
   double v[5] = {r2.get(), y2.get(), ys.get(), d0.get(), d1.get()};
   const int nv = 3 + nd;
   for (int c = 0; c < nv; ++c) {
-    const double s = block_sum(v[c], sm);
-    if (threadIdx.x == 0) a.partials[(long long)c * a.stride + blockIdx.x] = s;
+    const double sum = block_sum(v[c], sm);
+    if (threadIdx.x == 0) a.partials[(long long)c * a.stride + tix] = sum;
   }
   if (last_cta(&u.cnt, u.ntile)) {
     final_reduce(a.partials, a.stride, u.tile0, u.ntile, nv, out);
@@ -549,37 +611,62 @@ __global__ void __launch_bounds__(RSB_BLOCK) k_lz_resid(LzArgs<V> a, const V* __
         if (st != U_ACTIVE) {
           u.status = st;
           atomicSub(a.n_active, 1);
+        } else if (u.kk > 0) {
+          // thick restart: the kept Ritz vectors occupy q_0..q_{kk-1}; the next
+          // cycle starts at step kk from the residual direction
+          u.beta0 = u.beta[u.msteps];
+          u.j0 = u.kk;
+          u.msteps = u.m;
+          atomicMin(a.jmin, u.kk);
+        } else {
+          u.j0 = 0;  // explicit restart from y (proj2/proj3 follow)
+          atomicMin(a.jmin, 0);
+        }
+      }
+    }
+    if (mode == 0) {
+      __syncthreads();
+      // next cycle's S = diag(kept Ritz values); explicit restarts clear it all
+      if (u.status == U_ACTIVE) {
+        double* Sm = unit_S(a.S, t.unit);
+        const int kk = u.kk;
+        for (int idx = threadIdx.x; idx < RSB_MAXM * RSB_MAXM; idx += RSB_BLOCK) {
+          const int i = idx / RSB_MAXM, k = idx % RSB_MAXM;
+          Sm[idx] = (i == k && i < kk) ? u.th[i] : 0.0;
         }
       }
     }
   }
 }
 
-// y -= B cp (in place); dots of the result against B -> c2.
-template <typename V>
-__global__ void __launch_bounds__(RSB_BLOCK) k_proj2(LzArgs<V> a, V* __restrict__ y) {
-  __shared__ double sm[RSB_WARPS];
-  __shared__ double out[1 + RSB_MAXD];
-  const Tile t = a.tiles[blockIdx.x];
+// Explicit restart only (a cycle that ended on an invariant subspace without
+// converging): y -= B cp (in place); dots of the result against B -> c2.
+template <typename V, bool CO>
+__device__ __forceinline__ void proj2_t(const LzArgs<V>& a, V* y, int tix, double* sm,
+                                        double* out) {
+  const Tile t = a.tiles[tix];
   Unit& u = a.units[t.unit];
-  if (u.status != U_ACTIVE) return;
+  if (ldc<CO>(&u.status) != U_ACTIVE || ldc<CO>(&u.j0) != 0) return;
   const int nd = u.nd;
+  const double cp0 = ldc<CO>(&u.cp[0]), cp1 = ldc<CO>(&u.cp[1]), cp2 = ldc<CO>(&u.cp[2]);
   Acc<V> ys, d0, d1;
   for (int r = t.row0 + threadIdx.x; r < t.row1; r += RSB_BLOCK) {
     V v = y[r];
-    if (unit_has(u, a.ckey, r)) v -= V(u.cp[0] * u.isn);
-    if (nd > 0) v -= V(u.cp[1]) * V(a.D0[r]);
-    if (nd > 1) v -= V(u.cp[2]) * V(a.D1[r]);
+    if (unit_has(u, a.ckey, r)) v -= V(cp0 * u.isn);
+    if (nd > 0) v -= V(cp1) * V(a.D0[r]);
+    if (nd > 1) v -= V(cp2) * V(a.D1[r]);
     y[r] = v;
     ys.add(v);
     if (nd > 0) d0.add(V(a.D0[r]) * v);
     if (nd > 1) d1.add(V(a.D1[r]) * v);
   }
+  if (CO && a.pb_a && threadIdx.x == 0)
+    atomicAdd(a.pb_a, (unsigned long long)(t.row1 - t.row0) * (2 * sizeof(V) + 8ull * nd));
   double v[3] = {ys.get(), d0.get(), d1.get()};
   const int nv = 1 + nd;
   for (int c = 0; c < nv; ++c) {
-    const double s = block_sum(v[c], sm);
-    if (threadIdx.x == 0) a.partials[(long long)c * a.stride + blockIdx.x] = s;
+    const double sum = block_sum(v[c], sm);
+    if (threadIdx.x == 0) a.partials[(long long)c * a.stride + tix] = sum;
   }
   if (last_cta(&u.cnt, u.ntile)) {
     final_reduce(a.partials, a.stride, u.tile0, u.ntile, nv, out);
@@ -590,33 +677,101 @@ __global__ void __launch_bounds__(RSB_BLOCK) k_proj2(LzArgs<V> a, V* __restrict_
   }
 }
 
-// w0 = y - B c2 (second pass), beta0 = ||w0||; new cycle starts.
-template <typename V>
-__global__ void __launch_bounds__(RSB_BLOCK) k_proj3(LzArgs<V> a, const V* __restrict__ y) {
-  __shared__ double sm[RSB_WARPS];
-  __shared__ double out[1];
-  const Tile t = a.tiles[blockIdx.x];
+// w0 = y - B c2 (second pass), beta0 = ||w0||; a cycle starts at step 0.
+template <typename V, bool CO>
+__device__ __forceinline__ void proj3_t(const LzArgs<V>& a, const V* y, int tix, double* sm,
+                                        double* out) {
+  const Tile t = a.tiles[tix];
   Unit& u = a.units[t.unit];
-  if (u.status != U_ACTIVE) return;
+  if (ldc<CO>(&u.status) != U_ACTIVE || ldc<CO>(&u.j0) != 0) return;
   const int nd = u.nd;
+  const double c20 = ldc<CO>(&u.c2[0]), c21 = ldc<CO>(&u.c2[1]), c22 = ldc<CO>(&u.c2[2]);
   Acc<V> acc;
   for (int r = t.row0 + threadIdx.x; r < t.row1; r += RSB_BLOCK) {
     V v = y[r];
-    if (unit_has(u, a.ckey, r)) v -= V(u.c2[0] * u.isn);
-    if (nd > 0) v -= V(u.c2[1]) * V(a.D0[r]);
-    if (nd > 1) v -= V(u.c2[2]) * V(a.D1[r]);
+    if (unit_has(u, a.ckey, r)) v -= V(c20 * u.isn);
+    if (nd > 0) v -= V(c21) * V(a.D0[r]);
+    if (nd > 1) v -= V(c22) * V(a.D1[r]);
     a.W0[r] = v;
     acc.add(v * v);
   }
-  const double s = block_sum(acc.get(), sm);
-  if (threadIdx.x == 0) a.partials[blockIdx.x] = s;
+  if (CO && a.pb_a && threadIdx.x == 0)
+    atomicAdd(a.pb_a, (unsigned long long)(t.row1 - t.row0) * (2 * sizeof(V) + 8ull * nd));
+  const double sum = block_sum(acc.get(), sm);
+  if (threadIdx.x == 0) a.partials[tix] = sum;
   if (last_cta(&u.cnt, u.ntile)) {
     final_reduce(a.partials, a.stride, u.tile0, u.ntile, 1, out);
     if (threadIdx.x == 0) {
       u.beta0 = sqrt(out[0]);
       u.msteps = u.m;
+      u.broke = 0;
     }
   }
+}
+
+template <typename V>
+__global__ void __launch_bounds__(RSB_BLOCK) k_lz_ritz(LzArgs<V> a) {
+  lz_ritz_t<V, false>(a, blockIdx.x);
+}
+template <typename V>
+__global__ void __launch_bounds__(RSB_BLOCK) k_lz_resid(LzArgs<V> a, const V* __restrict__ y,
+                                                        int mode) {
+  __shared__ double sm[RSB_WARPS];
+  __shared__ double out[3 + RSB_MAXD];
+  lz_resid_t<V, false>(a, y, mode, blockIdx.x, sm, out);
+}
+template <typename V>
+__global__ void __launch_bounds__(RSB_BLOCK) k_proj2(LzArgs<V> a, V* __restrict__ y) {
+  __shared__ double sm[RSB_WARPS];
+  __shared__ double out[1 + RSB_MAXD];
+  proj2_t<V, false>(a, y, blockIdx.x, sm, out);
+}
+template <typename V>
+__global__ void __launch_bounds__(RSB_BLOCK) k_proj3(LzArgs<V> a, const V* __restrict__ y) {
+  __shared__ double sm[RSB_WARPS];
+  __shared__ double out[1];
+  proj3_t<V, false>(a, y, blockIdx.x, sm, out);
+}
+
+// ----------------------------------------------------------------------------
+// Persistent cooperative kernel: one whole Lanczos cycle (steps j0..M-1, the
+// Ritz pairs of S, Ritz vector and restart basis, residual) in one launch.
+// CTAs walk the tiles grid-stride (the same CTA owns the same tiles in every
+// phase); phases are separated by the bounded grid barrier; reductions keep
+// the last-CTA scheme, whose result the barrier publishes.
+// ----------------------------------------------------------------------------
+template <typename V>
+union CycleShared {
+  JacShared<V> J;
+  double wsd[SUBROWS];
+};
+
+template <typename V>
+__global__ void __launch_bounds__(RSB_BLOCK, 2)
+    k_lz_cycle(LzArgs<V> a, int jstart, int M, double breakdown, int ntiles, int nunits,
+               GridBar* gb) {
+  __shared__ CycleShared<V> sh;
+  __shared__ double out[RSB_MAXC];
+  __shared__ double sm[RSB_WARPS];
+  V* ws = reinterpret_cast<V*>(sh.wsd);
+  const unsigned G = gridDim.x;
+  for (int j = jstart; j < M; ++j) {
+    for (int t = blockIdx.x; t < ntiles; t += G) lz_a_t<V, true>(a, j, t, ws, out);
+    if (!grid_sync(gb, G)) return;
+    for (int t = blockIdx.x; t < ntiles; t += G) lz_b_t<V, true>(a, j, t, ws, out);
+    if (!grid_sync(gb, G)) return;
+    for (int t = blockIdx.x; t < ntiles; t += G) lz_c_t<V, true>(a, j, breakdown, t, sm, out);
+    if (!grid_sync(gb, G)) return;
+  }
+  for (int u = blockIdx.x; u < nunits; u += G) lz_eig_u<V, true>(a.units[u], unit_S(a.S, u), sh.J);
+  if (!grid_sync(gb, G)) return;
+  for (int t = blockIdx.x; t < ntiles; t += G) lz_ritz_t<V, true>(a, t);
+  if (!grid_sync(gb, G)) return;
+  for (int t = blockIdx.x; t < ntiles; t += G) lz_resid_t<V, true>(a, a.Y, 0, t, sm, out);
+  if (!grid_sync(gb, G)) return;
+  for (int t = blockIdx.x; t < ntiles; t += G) proj2_t<V, true>(a, a.Y, t, sm, out);
+  if (!grid_sync(gb, G)) return;
+  for (int t = blockIdx.x; t < ntiles; t += G) proj3_t<V, true>(a, a.Y, t, sm, out);
 }
 
 // Start vector into Y: hash of gid on unit rows (or a given vector), 0 elsewhere.
@@ -644,7 +799,7 @@ __global__ void __launch_bounds__(RSB_BLOCK) k_start(LzArgs<V> a, uint64_t sd, c
 // it is valid, its space orthogonal to 1 and the deflation vectors is not
 // empty, and (nd > 0) it found a cluster of size nd so far.
 __global__ void k_solve_init(Unit* units, int nunits, int nd, int krylov, int maxcycles, double tol,
-                             int require_cluster, int* n_active) {
+                             int require_cluster, int keep, int* n_active) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= nunits) return;
   Unit& u = units[i];
@@ -656,6 +811,10 @@ __global__ void k_solve_init(Unit* units, int nunits, int nd, int krylov, int ma
   u.nd = nd;
   u.m = (int)min((long long)krylov, dim);
   u.msteps = u.m;
+  u.j0 = 0;
+  u.kk = 0;
+  u.broke = 0;
+  u.keep = keep;
   u.cycles = 0;
   u.maxcycles = maxcycles;
   u.tolabs = tol * u.dmax;
@@ -697,24 +856,30 @@ static LzArgs<V> make_args(const LevelGraph& G, const Tile* tiles, int ntiles, U
   a.pb_a = prof_bytes(PROF_LZ_A);
   a.pb_b = prof_bytes(PROF_LZ_B);
   a.pb_c = prof_bytes(PROF_LZ_C);
+  if (prof_family() == PROF_CYCLE) a.pb_a = a.pb_b = a.pb_c = prof_bytes(PROF_CYCLE);
   a.pb_cg = prof_bytes(PROF_CG_AP);
+  a.S = B.S;
+  a.jmin = B.jmin;
   return a;
 }
 
 int solver_setup(Unit* units, int nunits, int nd, int krylov, int maxcycles, double tol,
-                 int require_cluster, SolveBufs& B, cudaStream_t s) {
+                 int require_cluster, int keep, SolveBufs& B, cudaStream_t s) {
   RSB_CK(cudaMemsetAsync(B.n_active, 0, sizeof(int), s));
   k_solve_init<<<(nunits + 127) / 128, 128, 0, s>>>(units, nunits, nd, krylov, maxcycles, tol,
-                                                    require_cluster, B.n_active);
+                                                    require_cluster, keep, B.n_active);
   RSB_CKL("k_solve_init");
   return RSB_OK;
 }
 
 static int read_active(SolveBufs& B, cudaStream_t s, int* out) {
   RSB_CK(cudaMemcpyAsync(B.h_active, B.n_active, sizeof(int), cudaMemcpyDeviceToHost, s));
+  if (B.jmin) RSB_CK(cudaMemcpyAsync(B.h_active + 2, B.jmin, sizeof(int), cudaMemcpyDeviceToHost, s));
+  if (B.gb) RSB_CK(cudaMemcpyAsync(B.h_active + 1, &B.gb->err, sizeof(int), cudaMemcpyDeviceToHost, s));
   RSB_CK(cudaStreamSynchronize(s));
   prof_collect();
   *out = *B.h_active;
+  if (B.gb && B.h_active[1]) return rsb_set_error(RSB_ETIMEOUT, "grid barrier wait gave up");
   return RSB_OK;
 }
 
@@ -739,19 +904,17 @@ static int lz_cycle(LzArgs<V>& a, int ntiles, int nunits, int M, double breakdow
     k_lz_a<V><<<ntiles, RSB_BLOCK, 0, s>>>(a, j);
     RSB_CKL("k_lz_a");
     prof_after(pi, s);
-    if (j + 1 < M) {
-      pi = prof_before(PROF_LZ_B, s);
-      k_lz_b<V><<<ntiles, RSB_BLOCK, 0, s>>>(a, j);
-      RSB_CKL("k_lz_b");
-      prof_after(pi, s);
-      pi = prof_before(PROF_LZ_C, s);
-      k_lz_c<V><<<ntiles, RSB_BLOCK, 0, s>>>(a, j, breakdown);
-      RSB_CKL("k_lz_c");
-      prof_after(pi, s);
-    }
+    pi = prof_before(PROF_LZ_B, s);
+    k_lz_b<V><<<ntiles, RSB_BLOCK, 0, s>>>(a, j);
+    RSB_CKL("k_lz_b");
+    prof_after(pi, s);
+    pi = prof_before(PROF_LZ_C, s);
+    k_lz_c<V><<<ntiles, RSB_BLOCK, 0, s>>>(a, j, breakdown);
+    RSB_CKL("k_lz_c");
+    prof_after(pi, s);
   }
-  k_lz_tridiag<<<nunits, 32, 0, s>>>(a.units, nunits);
-  RSB_CKL("k_lz_tridiag");
+  k_lz_eig<V><<<nunits, RSB_BLOCK, 0, s>>>(a.units, a.S, nunits);
+  RSB_CKL("k_lz_eig");
   k_lz_ritz<V><<<ntiles, RSB_BLOCK, 0, s>>>(a);
   RSB_CKL("k_lz_ritz");
   k_lz_resid<V><<<ntiles, RSB_BLOCK, 0, s>>>(a, a.Y, 0);
@@ -777,6 +940,31 @@ static int lanczos_run(const LevelGraph& G, const Tile* tiles, int ntiles, Unit*
   rc = lz_start<V>(a, ntiles, sd, from64, from32, s);
   if (rc) return rc;
   const double breakdown = 1e-14;
+  if (use_graph == 2 && B.gb) {
+    // one persistent cooperative launch per cycle
+    int dev = 0, nsm = 0, occ = 0;
+    RSB_CK(cudaGetDevice(&dev));
+    RSB_CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    RSB_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_lz_cycle<V>, RSB_BLOCK, 0));
+    const int grid = std::max(1, std::min(ntiles, occ * nsm));
+    GridBar* gb = B.gb;
+    int jstart = 0;
+    for (int cyc = 0; cyc < 100000; ++cyc) {
+      RSB_CK(cudaMemsetAsync(B.jmin, 0x7F, sizeof(int), s));
+      void* args[] = {(void*)&a, (void*)&jstart, (void*)&M, (void*)&breakdown, (void*)&ntiles,
+                      (void*)&nunits, (void*)&gb};
+      const int pi = prof_before(PROF_CYCLE, s);
+      cudaError_t e = cudaLaunchCooperativeKernel((const void*)k_lz_cycle<V>, grid, RSB_BLOCK,
+                                                  args, 0, s);
+      rsb_count_launch(1);
+      if (e != cudaSuccess) return rsb_set_cuda_error(e, "cudaLaunchCooperativeKernel(k_lz_cycle)");
+      prof_after(pi, s);
+      rc = read_active(B, s, &active);
+      if (rc || active == 0) break;
+      jstart = std::min(std::max(B.h_active[2], 0), M);
+    }
+    return rc;
+  }
   cudaGraphExec_t exec = nullptr;
   std::vector<int> cap_pairs;
   if (use_graph) {

@@ -38,7 +38,8 @@ class rsb_options(C.Structure):
                 ("cg_maxit", C.c_int), ("max_outer", C.c_int), ("seed", C.c_uint64),
                 ("degenerate_policy", C.c_int), ("cluster_tol", C.c_double),
                 ("tie_rel", C.c_double), ("mixed_tol", C.c_double), ("batched", C.c_int),
-                ("use_graph", C.c_int), ("validate", C.c_int), ("polish_cycles", C.c_int)]
+                ("use_graph", C.c_int), ("validate", C.c_int), ("polish_cycles", C.c_int),
+                ("keep", C.c_int), ("tile_rows", C.c_int)]
 
 
 class rsb_stats(C.Structure):
@@ -298,7 +299,7 @@ def rsb_release():
     load().rsb_release()
 
 
-PROFILE_FAMILIES = {"lz_a": 1, "lz_b": 2, "lz_c": 3, "cg_ap": 4, "spmv": 5}
+PROFILE_FAMILIES = {"lz_a": 1, "lz_b": 2, "lz_c": 3, "cg_ap": 4, "spmv": 5, "cycle": 6}
 
 
 def rsb_profile_begin(family: str | int):

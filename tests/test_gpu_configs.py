@@ -1,0 +1,132 @@
+"""Full-size configurations, checked where the oracle can follow.
+
+* C3: 192x128x96 box, 10% seeded deletion, largest component, vertex adjacency
+  (4/2/1), inverse iteration with CG (FP32 vectors, FP64 alpha/beta), 256 parts;
+  the FP32 vector is polished by FP64 Lanczos cycles (on 26-neighbour graphs
+  the Rayleigh quotient of an FP32-accurate vector alone misses the 1e-6
+  bound on lambda_2).
+* C4: 512 boxes with sides drawn from [8, 96], face adjacency, 16 parts each, one
+  batched call per level.
+* C5: 256^3 box, 5% deletion, vertex adjacency, mixed Lanczos, 1024 parts.
+
+At these sizes the oracle checks sampled outputs one by one: it applies its own
+Laplacian to the library's Fiedler vector (residual and Rayleigh quotient), it
+fixes the exact part sizes (R6), and it partitions small meshes of the C4 batch
+completely.  Closed-form meshes of the batch must match bit for bit.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from meshgen import batch_box_dims, box_graph, box_graph_deleted
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("no GPU", allow_module_level=True)
+
+import paper_2606_14659_gb300 as R  # noqa: E402
+
+
+def _sizes_ok(part, n, P):
+    sizes = np.bincount(part, minlength=P)
+    return np.array_equal(sizes, [O.seg_size(p, p + 1, n, P) for p in range(P)])
+
+
+def _check_fiedler_with_oracle(g, lam, v, rel=1e-5):
+    """The oracle's own Laplacian: v is a unit vector orthogonal to 1, its
+    Rayleigh quotient equals lam and its residual is within rel * d_max."""
+    v = np.asarray(v, dtype=np.float64)
+    lv = O.laplacian_apply(g, v)
+    dmax = O.degree(g).max()
+    assert abs(np.linalg.norm(v) - 1.0) < 1e-6
+    assert abs(v.sum()) < 1e-6 * np.sqrt(g.n)
+    rq = float(v @ lv)
+    assert abs(rq - lam) <= 1e-6 * lam
+    assert np.linalg.norm(lv - lam * v) <= rel * dmax
+    return rq
+
+
+@pytest.fixture(scope="module")
+def c3():
+    return box_graph_deleted(192, 128, 96, 0.10, 20260, "vertex")
+
+
+def test_c3_fiedler_inverse_mixed_vs_oracle_checks(c3):
+    G = R.graph(c3)
+    lam, v, res, code = R.rsb_fiedler(G, R.options(method="inverse", precision="mixed",
+                                                   degenerate_policy="none", polish_cycles=8))
+    assert code in (0, R.rsb.RSB_ENOCONV)
+    _check_fiedler_with_oracle(c3, lam, v.cpu().numpy())
+    lam64, v64, res64, _ = R.rsb_fiedler(G, R.options(method="inverse", precision="fp64"))
+    assert abs(lam64 - lam) <= 1e-6 * lam64
+    _check_fiedler_with_oracle(c3, lam64, v64.cpu().numpy(), rel=1e-8)
+
+
+def test_c3_partition_inverse_mixed(c3):
+    G = R.graph(c3)
+    part, st, code = R.rsb_partition(G, 256, R.options(method="inverse", precision="mixed",
+                                                       degenerate_policy="none",
+                                                       polish_cycles=8))
+    part = part.cpu().numpy()
+    assert _sizes_ok(part, c3.n, 256)
+    assert st["levels"] == 8
+    m = O.partition_metrics(c3, part, 256)
+    # quality of the paper's kind (§8): a 26-neighbour mesh keeps neighbour counts bounded
+    assert m["max_neighbours"] <= 40
+    assert st["resid_max"] <= 1e-5
+
+
+@pytest.fixture(scope="module")
+def c4():
+    dims = batch_box_dims(512, 8, 96, 2026)
+    return dims, [box_graph(*d) for d in dims]
+
+
+def test_c4_batch_sizes_clean_meshes_and_small_meshes_vs_oracle(c4):
+    dims, gs = c4
+    parts, st, code = R.rsb_partition_batch([R.graph(g) for g in gs], [16] * len(gs),
+                                            R.options(precision="mixed"))
+    parts = [p.cpu().numpy() for p in parts]
+    assert st["levels"] == 4
+    clean = 0
+    for d, g, p in zip(dims, gs, parts):
+        assert _sizes_ok(p, g.n, 16)
+        try:
+            cf = O.box_partition_closed_form(*d, 16)
+        except O.NotClean:
+            continue
+        clean += 1
+        assert np.array_equal(p, cf), d
+    assert clean >= 30
+    # the smallest meshes, partitioned completely by the oracle
+    order = np.argsort([g.n for g in gs])[:2]
+    for i in order:
+        ref = O.rsb_partition(gs[i], 16)
+        mr = O.partition_metrics(gs[i], ref, 16)["weighted_cut"]
+        mg = O.partition_metrics(gs[i], parts[i], 16)["weighted_cut"]
+        assert mg <= 1.02 * mr, (dims[i], mg, mr)
+
+
+def test_c4_batch_equals_separate_calls(c4):
+    dims, gs = c4
+    pick = [0, 7, 100, 511]
+    parts, _, _ = R.rsb_partition_batch([R.graph(gs[i]) for i in pick], [16] * len(pick),
+                                        R.options(precision="mixed"))
+    for i, p in zip(pick, parts):
+        alone, _, _ = R.rsb_partition(R.graph(gs[i]), 16, R.options(precision="mixed"))
+        assert np.array_equal(p.cpu().numpy(), alone.cpu().numpy())
+
+
+def test_c5_partition_mixed_lanczos():
+    g = box_graph_deleted(256, 256, 256, 0.05, 20261, "vertex")
+    G = R.graph(g)
+    opts = R.options(precision="mixed", degenerate_policy="none", polish_cycles=8)
+    lam, v, res, code = R.rsb_fiedler(G, opts)
+    _check_fiedler_with_oracle(g, lam, v.cpu().numpy())
+    part, st, code = R.rsb_partition(G, 1024, opts)
+    part = part.cpu().numpy()
+    assert _sizes_ok(part, g.n, 1024)
+    assert st["levels"] == 10
+    assert abs(st["lambda_first"] - lam) <= 1e-6 * lam

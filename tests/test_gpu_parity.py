@@ -106,6 +106,17 @@ def test_fiedler_mixed_polish_reaches_fp64(polish):
     assert res <= 1e-9 * O.degree(g).max()
 
 
+@pytest.mark.parametrize("keep", [0, 4, 8, 16])
+def test_thick_restart_sizes_agree_with_oracle(keep):
+    g = box_graph(25, 22, 12)
+    ref = O.fiedler_of_graph(g, O.Options(keep=keep))
+    lam, v, res, code = R.rsb_fiedler(R.graph(g), R.options(keep=keep))
+    assert abs(lam - ref[0]) <= 1e-9 * ref[0]
+    assert np.abs(_np(v) - ref[1]).max() < 1e-6
+    if keep:
+        assert ref[2].converged and code == 0
+
+
 @pytest.mark.parametrize("seed", [0, 1, 2])
 def test_fiedler_random_vs_oracle(seed):
     g = random_graph(300, 700, 40 + seed)
@@ -143,7 +154,7 @@ def _closed_c1():
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
 @pytest.mark.parametrize("batched", [1, 0])
-@pytest.mark.parametrize("use_graph", [1, 0])
+@pytest.mark.parametrize("use_graph", [2, 1, 0])
 def test_partition_c1_closed_form(precision, batched, use_graph):
     g = box_graph(16, 8, 4)
     part, st, code = R.rsb_partition(R.graph(g), 8, R.options(precision=precision, batched=batched,
@@ -275,9 +286,11 @@ def _closed_c2():
 
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
-def test_partition_c2_closed_form(precision):
+@pytest.mark.parametrize("use_graph", [2, 1])
+def test_partition_c2_closed_form(precision, use_graph):
     g = box_graph(64, 64, 32)
-    part, st, code = R.rsb_partition(R.graph(g), 64, R.options(precision=precision))
+    part, st, code = R.rsb_partition(R.graph(g), 64, R.options(precision=precision,
+                                                                use_graph=use_graph))
     assert np.array_equal(_np(part), _closed_c2())
     assert st["levels"] == 6
     assert abs(st["lambda_first"] - O.box_lambda2(64, 64, 32)) <= 1e-6 * O.box_lambda2(64, 64, 32)
