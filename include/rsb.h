@@ -93,12 +93,14 @@ typedef struct rsb_options {
                             1 one CUDA graph per cycle, 2 one persistent cooperative
                             kernel per cycle (CG blocks use a CUDA graph for 1 and 2) */
   int validate;          /* 1: also check symmetry of the input on the device      */
-  int polish_cycles;     /* MIXED: FP64 Lanczos cycles after the FP32 stage (0: only
+  int polish_cycles;     /* MIXED: at most this many FP64 Lanczos cycles of polish_dim
+                            steps after the FP32 stage, stopping early at tol (0: only
                             the FP64 Rayleigh-quotient refinement of the FP32 vector) */
   int keep;              /* Ritz vectors kept by a thick restart, 0..16 (0: restart
                             from the Ritz vector alone)                               */
   int tile_rows;         /* rows per thread of a solver tile (a tile is 256 x this
                             many rows of one subgraph), 1..64; 0: the default 2     */
+  int polish_dim;        /* MIXED: Lanczos steps per FP64 polish cycle, 2..40      */
 } rsb_options;
 
 typedef struct rsb_stats {
@@ -117,7 +119,7 @@ typedef struct rsb_stats {
 /* Fills *o with the defaults: Lanczos, FP64, krylov_dim 40, max_restarts 50,
  * tol 1e-10, cg_tol 1e-12, cg_maxit 4000, max_outer 50, RESOLVE,
  * cluster_tol 0.05, tie_rel 1e-5, mixed_tol 1e-6, batched 1, use_graph 1,
- * validate 0, polish_cycles 0, keep 8, tile_rows 0. */
+ * validate 0, polish_cycles 2, keep 8, tile_rows 0, polish_dim 16. */
 void rsb_options_default(rsb_options *o);
 
 /*

@@ -57,7 +57,8 @@ int solver_inverse(const LevelGraph& G, const Tile* tiles, int ntiles, Unit* uni
                    cudaStream_t s);
 int solver_write_vector(const LevelGraph& G, const Tile* tiles, int ntiles, Unit* units,
                         const uint64_t* ckey, SolveBufs& B, int f32, int from_x, double* out,
-                        int cand, cudaStream_t s);
+                        int cand, int better_only, cudaStream_t s);
+int solver_keep_better(Unit* units, int nunits, int cand, double tol1, cudaStream_t s);
 int solver_quartic(const Tile* tiles, int ntiles, Unit* units, int nunits, const uint64_t* ckey,
                    double* v0, double* v1, double* v2, double* partials, double* mom,
                    cudaStream_t s);
@@ -313,9 +314,10 @@ extern "C" void rsb_options_default(rsb_options* o) {
   o->batched = 1;
   o->use_graph = 1;
   o->validate = 0;
-  o->polish_cycles = 0;
+  o->polish_cycles = 2;
   o->keep = 8;
   o->tile_rows = 0;
+  o->polish_dim = 16;
 }
 
 static int check_options(const rsb_options& o) {
@@ -325,6 +327,7 @@ static int check_options(const rsb_options& o) {
   if (o.krylov_dim < 1 || o.krylov_dim > RSB_MAXM) return rsb_set_error(RSB_EINVAL, "krylov_dim");
   if (o.keep < 0 || o.keep > RSB_MAXKEEP) return rsb_set_error(RSB_EINVAL, "keep");
   if (o.tile_rows < 0 || o.tile_rows > 64) return rsb_set_error(RSB_EINVAL, "tile_rows");
+  if (o.polish_dim < 2 || o.polish_dim > RSB_MAXM) return rsb_set_error(RSB_EINVAL, "polish_dim");
   if (o.max_restarts < 1) return rsb_set_error(RSB_EINVAL, "max_restarts");
   if (!(o.tol > 0) || !(o.cg_tol > 0) || !(o.mixed_tol > 0))
     return rsb_set_error(RSB_EINVAL, "tolerances");
@@ -538,26 +541,14 @@ static int solve_candidate(Ctx& c, const LevelGraph& G, const Tile* tiles, int n
   if (rc) return rc;
   const void* stage1_vec = inverse ? B.X : B.Y;
   if (!mixed) {
-    if ((rc = solver_write_vector(G, tiles, ntiles, units, ckey, B, 0, inverse, out, cand, c.s)))
-      return rc;
-  } else if (o.polish_cycles > 0) {
-    // stage 2: a bounded number of FP64 Lanczos cycles started from the FP32 vector
-    SolveBufs B64 = B;
-    if ((rc = reserve_prec(c, 0, G.n, std::max(M, 1), B64))) return rc;
-    B64.D[0] = B.D[0];
-    B64.D[1] = B.D[1];
-    if ((rc = solver_setup(units, nunits, nd, o.krylov_dim, o.polish_cycles, o.tol,
-                           require_cluster, o.keep, B64, c.s)))
-      return rc;
-    if ((rc = solver_lanczos(G, tiles, ntiles, units, nunits, ckey, B64, 0, M, sd, nullptr,
-                             (const float*)stage1_vec, use_graph, c.s)))
-      return rc;
-    if ((rc = solver_write_vector(G, tiles, ntiles, units, ckey, B64, 0, 0, out, cand, c.s)))
+    if ((rc = solver_write_vector(G, tiles, ntiles, units, ckey, B, 0, inverse, out, cand, 0,
+                                  c.s)))
       return rc;
   } else {
     // stage 2: FP64 Rayleigh-quotient refinement of the FP32 vector
     SolveBufs B64 = B;
-    if ((rc = reserve_prec(c, 0, G.n, 1, B64))) return rc;
+    const int Mp = (int)std::min<int64_t>(o.polish_dim, dim);
+    if ((rc = reserve_prec(c, 0, G.n, o.polish_cycles > 0 ? std::max(Mp, 1) : 1, B64))) return rc;
     B64.D[0] = B.D[0];
     B64.D[1] = B.D[1];
     if ((rc = solver_setup(units, nunits, nd, o.krylov_dim, 1, tol1, require_cluster, o.keep, B64,
@@ -566,8 +557,22 @@ static int solve_candidate(Ctx& c, const LevelGraph& G, const Tile* tiles, int n
     if ((rc = solver_rq_refine(G, tiles, ntiles, units, nunits, ckey, B64,
                                (const float*)stage1_vec, c.s)))
       return rc;
-    if ((rc = solver_write_vector(G, tiles, ntiles, units, ckey, B64, 0, 1, out, cand, c.s)))
+    if ((rc = solver_write_vector(G, tiles, ntiles, units, ckey, B64, 0, 1, out, cand, 0, c.s)))
       return rc;
+    if (o.polish_cycles > 0) {
+      // stage 3: at most polish_cycles FP64 Lanczos cycles of polish_dim steps,
+      // started from the FP32 vector, stopping early at tol; a unit keeps the
+      // polished vector only where it lowered the FP64 residual
+      if ((rc = solver_setup(units, nunits, nd, o.polish_dim, o.polish_cycles, o.tol,
+                             require_cluster, o.keep, B64, c.s)))
+        return rc;
+      if ((rc = solver_lanczos(G, tiles, ntiles, units, nunits, ckey, B64, 0, Mp, sd, nullptr,
+                               (const float*)stage1_vec, use_graph, c.s)))
+        return rc;
+      if ((rc = solver_write_vector(G, tiles, ntiles, units, ckey, B64, 0, 0, out, cand, 1, c.s)))
+        return rc;
+      if ((rc = solver_keep_better(units, nunits, cand, tol1, c.s))) return rc;
+    }
   }
   // statistics
   RSB_CK(cudaMemsetAsync(&cn->capped, 0, sizeof(int), c.s));

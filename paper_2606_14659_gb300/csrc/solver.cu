@@ -1355,32 +1355,61 @@ int solver_rq_refine(const LevelGraph& G, const Tile* tiles, int ntiles, Unit* u
 // ----------------------------------------------------------------------------
 // result vector: out = y / ||y|| (FP64), for units that took part in the solve
 // ----------------------------------------------------------------------------
+// better_only: a polish result, written only where its residual is below the
+// one recorded for candidate cand (the refined stage-1 vector already in out);
+// k_keep_better then settles the unit's record.
 template <typename V>
 __global__ void __launch_bounds__(RSB_BLOCK) k_write_vec(LzArgs<V> a, const V* __restrict__ y,
-                                                         double* out, int cand) {
+                                                         double* out, int cand, int better_only) {
   const Tile t = a.tiles[blockIdx.x];
   Unit& u = a.units[t.unit];
   if (u.status != U_CONVERGED && u.status != U_CAPPED) return;
+  if (better_only && !(u.resid < u.res[cand])) return;
   const double sc = 1.0 / sqrt(u.ynorm2);
   for (int r = t.row0 + threadIdx.x; r < t.row1; r += RSB_BLOCK) out[r] = sc * (double)y[r];
-  if (blockIdx.x == u.tile0 && threadIdx.x == 0 && cand >= 0) {
+  if (!better_only && blockIdx.x == u.tile0 && threadIdx.x == 0 && cand >= 0) {
     u.lam[cand] = u.theta;
     u.res[cand] = u.resid;
   }
 }
 
+// After a polish: the unit keeps the smaller-residual of the refined stage-1
+// vector and the polished one (a capped polish can end on a Ritz vector whose
+// residual exceeds its start's); it counts as converged at tol1 * dmax.
+__global__ void k_keep_better(Unit* units, int nunits, int cand, double tol1) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nunits) return;
+  Unit& u = units[i];
+  if (u.status != U_CONVERGED && u.status != U_CAPPED) return;
+  if (u.resid < u.res[cand]) {
+    u.lam[cand] = u.theta;
+    u.res[cand] = u.resid;
+  } else {
+    u.theta = u.lam[cand];
+    u.resid = u.res[cand];
+  }
+  u.status = u.resid <= tol1 * u.dmax ? U_CONVERGED : U_CAPPED;
+}
+
 int solver_write_vector(const LevelGraph& G, const Tile* tiles, int ntiles, Unit* units,
                         const uint64_t* ckey, SolveBufs& B, int f32, int from_x, double* out,
-                        int cand, cudaStream_t s) {
+                        int cand, int better_only, cudaStream_t s) {
   if (ntiles <= 0) return RSB_OK;
   if (f32) {
     LzArgs<float> a = make_args<float>(G, tiles, ntiles, units, ckey, B);
-    k_write_vec<float><<<ntiles, RSB_BLOCK, 0, s>>>(a, from_x ? a.X : a.Y, out, cand);
+    k_write_vec<float><<<ntiles, RSB_BLOCK, 0, s>>>(a, from_x ? a.X : a.Y, out, cand, better_only);
   } else {
     LzArgs<double> a = make_args<double>(G, tiles, ntiles, units, ckey, B);
-    k_write_vec<double><<<ntiles, RSB_BLOCK, 0, s>>>(a, from_x ? a.X : a.Y, out, cand);
+    k_write_vec<double><<<ntiles, RSB_BLOCK, 0, s>>>(a, from_x ? a.X : a.Y, out, cand,
+                                                     better_only);
   }
   RSB_CKL("k_write_vec");
+  return RSB_OK;
+}
+
+int solver_keep_better(Unit* units, int nunits, int cand, double tol1, cudaStream_t s) {
+  k_keep_better<<<(nunits + 127) / 128, 128, 0, s>>>(units, nunits, cand, tol1);
+  RSB_CKL("k_keep_better");
   return RSB_OK;
 }
 

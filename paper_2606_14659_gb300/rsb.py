@@ -39,7 +39,7 @@ class rsb_options(C.Structure):
                 ("degenerate_policy", C.c_int), ("cluster_tol", C.c_double),
                 ("tie_rel", C.c_double), ("mixed_tol", C.c_double), ("batched", C.c_int),
                 ("use_graph", C.c_int), ("validate", C.c_int), ("polish_cycles", C.c_int),
-                ("keep", C.c_int), ("tile_rows", C.c_int)]
+                ("keep", C.c_int), ("tile_rows", C.c_int), ("polish_dim", C.c_int)]
 
 
 class rsb_stats(C.Structure):

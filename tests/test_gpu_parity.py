@@ -91,19 +91,32 @@ def test_fiedler_box(method, precision, dims):
         assert abs(lam - lam_ref) <= 1e-9 * lam_ref
         assert np.abs(_np(v) - vo).max() < 1e-6
         assert res <= 1e-10 * dmax * 1.01
-    else:  # FP32 stage + FP64 Rayleigh quotient: the mixed form's stated bar
+    else:  # FP32 stage + FP64 Rayleigh quotient + short polish: the mixed form's stated bar
         assert abs(lam - lam_ref) <= 1e-6 * lam_ref
         assert np.abs(_np(v) - vo).max() < 1e-4
         assert res <= 1e-5 * dmax
 
 
-@pytest.mark.parametrize("polish", [2, 6])
-def test_fiedler_mixed_polish_reaches_fp64(polish):
+@pytest.mark.parametrize("cycles,dim", [(2, 40), (50, 16)])
+def test_fiedler_mixed_polish_reaches_fp64(cycles, dim):
     g = box_graph(12, 7, 5)
     lam, v, res, code = R.rsb_fiedler(R.graph(g), R.options(precision="mixed",
-                                                             polish_cycles=polish))
+                                                             polish_cycles=cycles,
+                                                             polish_dim=dim))
     assert abs(lam - O.box_lambda2(12, 7, 5)) <= 1e-10 * O.box_lambda2(12, 7, 5)
     assert res <= 1e-9 * O.degree(g).max()
+
+
+def test_mixed_partition_resolves_tied_slab_like_oracle():
+    # 9x24x13 -> 16: after the 24-axis split the 13-axis median falls inside the
+    # middle slab, whose values tie (cos = 0); the tie must go by gid (R7) as in
+    # the oracle.  FP32 vectors alone order that slab by their error instead.
+    g = box_graph(9, 24, 13)
+    ref = O.rsb_partition(g, 16)
+    for prec in ("fp64", "mixed"):
+        part, st, code = R.rsb_partition(R.graph(g), 16, R.options(precision=prec))
+        assert code == 0
+        assert np.array_equal(_np(part), ref), prec
 
 
 @pytest.mark.parametrize("keep", [0, 4, 8, 16])
