@@ -91,7 +91,10 @@ typedef struct rsb_options {
   int batched;           /* 1: all subgraphs of a level in one set of launches     */
   int use_graph;         /* launch mode of a Lanczos cycle: 0 one launch per kernel,
                             1 one CUDA graph per cycle, 2 one persistent cooperative
-                            kernel per cycle (CG blocks use a CUDA graph for 1 and 2) */
+                            kernel per cycle, 3 one persistent cooperative kernel per
+                            solve whose CTAs keep their tile's basis rows in shared
+                            memory when every tile gets a co-resident CTA (else 1);
+                            CG blocks use a CUDA graph for 1, 2 and 3                */
   int validate;          /* 1: also check symmetry of the input on the device      */
   int polish_cycles;     /* MIXED: at most this many FP64 Lanczos cycles of polish_dim
                             steps after the FP32 stage, stopping early at tol (0: only

@@ -215,8 +215,9 @@ struct Ctx {
   DevBuf cand[3];
   PrecBufs pb[2];  // 0: FP64, 1: FP32
   DevBuf seg_row0, seg_nleft, seg_child0, seg_p0, seg_split, seg_keystar, seg_unit, seg_ncomp;
-  DevBuf counters;  // int flag, int n_active, int n_cg, long long cycles, int capped, double resid
+  DevBuf counters;  // one Counters record
   DevBuf part_concat;
+  int trmax = 0;    // largest tile of the level being solved, rows
   std::vector<DevBuf> stage;  // staged host inputs
   int* h_pinned = nullptr;
 };
@@ -254,8 +255,7 @@ struct Counters {
   long long cycles;
   double resid_max;
   GridBar gb;
-  int jmin;
-  int pad;
+  int jmin[2];
 };
 
 // ----------------------------------------------------------------------------
@@ -328,6 +328,7 @@ static int check_options(const rsb_options& o) {
   if (o.keep < 0 || o.keep > RSB_MAXKEEP) return rsb_set_error(RSB_EINVAL, "keep");
   if (o.tile_rows < 0 || o.tile_rows > 64) return rsb_set_error(RSB_EINVAL, "tile_rows");
   if (o.polish_dim < 2 || o.polish_dim > RSB_MAXM) return rsb_set_error(RSB_EINVAL, "polish_dim");
+  if (o.use_graph < 0 || o.use_graph > 3) return rsb_set_error(RSB_EINVAL, "use_graph");
   if (o.max_restarts < 1) return rsb_set_error(RSB_EINVAL, "max_restarts");
   if (!(o.tol > 0) || !(o.cg_tol > 0) || !(o.mixed_tol > 0))
     return rsb_set_error(RSB_EINVAL, "tolerances");
@@ -422,6 +423,12 @@ static int build_level0(Ctx& c, const std::vector<MeshIn>& meshes, int validate,
 // ----------------------------------------------------------------------------
 // tiles
 // ----------------------------------------------------------------------------
+static int max_tile_rows(const std::vector<Tile>& tiles) {
+  int m = 0;
+  for (const Tile& t : tiles) m = std::max(m, t.row1 - t.row0);
+  return m;
+}
+
 static void make_tiles(std::vector<Unit>& units, std::vector<Tile>& tiles, int rmin = RSB_MINR) {
   tiles.clear();
   for (size_t i = 0; i < units.size(); ++i) {
@@ -487,7 +494,7 @@ static int reserve_prec(Ctx& c, int f32, int64_t N, int M, SolveBufs& B) {
   B.stat_cycles = &cn->cycles;
   B.h_active = c.h_pinned + 4;
   B.gb = &cn->gb;
-  B.jmin = &cn->jmin;
+  B.jmin = cn->jmin;
   B.S = dptr<double>(c.sbuf);
   B.partials = dptr<double>(c.partials);
   return RSB_OK;
@@ -517,6 +524,7 @@ static int solve_candidate(Ctx& c, const LevelGraph& G, const Tile* tiles, int n
   const uint64_t* ckey = dptr<uint64_t>(c.ckey);
   int rc;
   SolveBufs B;
+  B.trmax = c.trmax;
   B.D[0] = nd > 0 ? dptr<double>(c.cand[0]) : nullptr;
   B.D[1] = nd > 1 ? dptr<double>(c.cand[1]) : nullptr;
   Counters* cn = dptr<Counters>(c.counters);
@@ -597,7 +605,7 @@ static int split_units(Ctx& c, const LevelGraph& G, std::vector<Unit>& hunits,
   int rc;
   if ((rc = devbuf_reserve(c.units, sizeof(Unit) * nunits))) return rc;
   if ((rc = devbuf_reserve(c.tiles, sizeof(Tile) * ntiles))) return rc;
-  if ((rc = devbuf_reserve(c.partials, sizeof(double) * (size_t)RSB_MAXC * ntiles + 64))) return rc;
+  if ((rc = devbuf_reserve(c.partials, 2 * sizeof(double) * (size_t)RSB_MAXC * ntiles + 64))) return rc;
   if ((rc = devbuf_reserve(c.hist, sizeof(int) * 256 * (size_t)nunits))) return rc;
   if ((rc = devbuf_reserve(c.mom, sizeof(double) * 24 * (size_t)nunits))) return rc;
   if ((rc = devbuf_reserve(c.sbuf, sizeof(double) * RSB_SSTRIDE * (size_t)nunits))) return rc;
@@ -608,6 +616,7 @@ static int split_units(Ctx& c, const LevelGraph& G, std::vector<Unit>& hunits,
   Tile* tiles = dptr<Tile>(c.tiles);
   RSB_CK(cudaMemcpyAsync(units, hunits.data(), sizeof(Unit) * nunits, cudaMemcpyHostToDevice, c.s));
   RSB_CK(cudaMemcpyAsync(tiles, htiles.data(), sizeof(Tile) * ntiles, cudaMemcpyHostToDevice, c.s));
+  c.trmax = max_tile_rows(htiles);
   const uint64_t* ckey = dptr<uint64_t>(c.ckey);
   double* partials = dptr<double>(c.partials);
   int64_t maxn = 0;
@@ -1118,10 +1127,11 @@ extern "C" int rsb_fiedler(const rsb_csr* g, const rsb_options* opt, double* lam
   u.isn = 1.0 / std::sqrt((double)N);
   std::vector<Tile> htiles;
   make_tiles(hunits, htiles, o.tile_rows > 0 ? o.tile_rows : RSB_MINR);
+  c.trmax = max_tile_rows(htiles);
   const int ntiles = (int)htiles.size();
   if ((rc = devbuf_reserve(c.units, sizeof(Unit))) ||
       (rc = devbuf_reserve(c.tiles, sizeof(Tile) * ntiles)) ||
-      (rc = devbuf_reserve(c.partials, sizeof(double) * (size_t)RSB_MAXC * ntiles + 64)) ||
+      (rc = devbuf_reserve(c.partials, 2 * sizeof(double) * (size_t)RSB_MAXC * ntiles + 64)) ||
       (rc = devbuf_reserve(c.sbuf, sizeof(double) * RSB_SSTRIDE)) ||
       (rc = devbuf_reserve(c.cand[0], sizeof(double) * (N + 32))))
     return end_call(c, stream, rc);

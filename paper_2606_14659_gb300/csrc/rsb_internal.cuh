@@ -424,6 +424,8 @@ struct SolveBufs {
   int* h_active = nullptr;       // pinned host word for read-backs
   struct GridBar* gb = nullptr;  // barrier of the persistent cycle kernel
   double* S = nullptr;           // per-unit projected matrices and Ritz vectors
-  int* jmin = nullptr;           // device: smallest next-cycle start step
+  int* jmin = nullptr;           // device: smallest next-cycle start step (2 slots)
   int64_t N = 0;
+  int trmax = 0;                 // largest tile of the level, rows
+  int maxcycles = 0;             // cycle cap of the current solve
 };

@@ -450,8 +450,9 @@ __device__ void lz_eig_u(Unit& u, double* Sm, JacShared<T>& J) {
     off = J.red[0];
     __syncthreads();
     if (off <= thr) break;
+    const int np = n2 / 2;
     for (int rnd = 0; rnd < n2 - 1; ++rnd) {
-      if (tid < n2 / 2) {
+      if (tid < np) {
         int pa = tid == 0 ? 0 : ((tid + rnd - 1) % (n2 - 1)) + 1;
         int pb = ((n2 - 1 - tid + rnd - 1) % (n2 - 1)) + 1;
         if (pa > pb) { const int tt = pa; pa = pb; pb = tt; }
@@ -470,25 +471,30 @@ __device__ void lz_eig_u(Unit& u, double* Sm, JacShared<T>& J) {
         J.s[tid] = ss;
       }
       __syncthreads();
-      for (int task = tid; task < (n2 / 2) * n2; task += RSB_BLOCK) {
-        const int i = task / n2, r = task % n2;
-        const int pa = J.p[i], pb = J.q[i];
-        const T cc = J.c[i], ss = J.s[i];
-        const T x = J.A[r][pa], y = J.A[r][pb];
-        J.A[r][pa] = cc * x - ss * y;
-        J.A[r][pb] = ss * x + cc * y;
-        const T zx = J.Z[r][pa], zy = J.Z[r][pb];
-        J.Z[r][pa] = cc * zx - ss * zy;
-        J.Z[r][pb] = ss * zx + cc * zy;
-      }
-      __syncthreads();
-      for (int task = tid; task < (n2 / 2) * n2; task += RSB_BLOCK) {
-        const int i = task / n2, col = task % n2;
-        const int pa = J.p[i], pb = J.q[i];
-        const T cc = J.c[i], ss = J.s[i];
-        const T x = J.A[pa][col], y = J.A[pb][col];
-        J.A[pa][col] = cc * x - ss * y;
-        J.A[pb][col] = ss * x + cc * y;
+      // the round's rotations act on disjoint index pairs, so every 2x2 block
+      // (pair i1 rows, pair i2 columns) is updated in place by one thread:
+      // the column rotation, then the row rotation; Z takes the column one
+      for (int task = tid; task < np * np + np * n2; task += RSB_BLOCK) {
+        if (task < np * np) {
+          const int i1 = task / np, i2 = task - i1 * np;
+          const int p1 = J.p[i1], q1 = J.q[i1], p2 = J.p[i2], q2 = J.q[i2];
+          const T c1 = J.c[i1], s1 = J.s[i1], c2 = J.c[i2], s2 = J.s[i2];
+          const T a11 = J.A[p1][p2], a12 = J.A[p1][q2], a21 = J.A[q1][p2], a22 = J.A[q1][q2];
+          const T b11 = c2 * a11 - s2 * a12, b12 = s2 * a11 + c2 * a12;
+          const T b21 = c2 * a21 - s2 * a22, b22 = s2 * a21 + c2 * a22;
+          J.A[p1][p2] = c1 * b11 - s1 * b21;
+          J.A[q1][p2] = s1 * b11 + c1 * b21;
+          J.A[p1][q2] = c1 * b12 - s1 * b22;
+          J.A[q1][q2] = s1 * b12 + c1 * b22;
+        } else {
+          const int zt = task - np * np;
+          const int i = zt / n2, r = zt - i * n2;
+          const int pa = J.p[i], pb = J.q[i];
+          const T cc = J.c[i], ss = J.s[i];
+          const T zx = J.Z[r][pa], zy = J.Z[r][pb];
+          J.Z[r][pa] = cc * zx - ss * zy;
+          J.Z[r][pb] = ss * zx + cc * zy;
+        }
       }
       __syncthreads();
     }
@@ -774,6 +780,281 @@ __global__ void __launch_bounds__(RSB_BLOCK, 2)
   for (int t = blockIdx.x; t < ntiles; t += G) proj3_t<V, true>(a, a.Y, t, sm, out);
 }
 
+// ----------------------------------------------------------------------------
+// Resident persistent solve (launch mode 3).  When every tile of the level can
+// own one co-resident CTA and the tile's rows of the basis fit in that CTA's
+// shared memory (the level's basis is at most the chip's shared memory: the
+// 131,072-row level with 40 FP32 vectors is 21 MB over 256 CTAs), one
+// cooperative launch runs every cycle of the solve.  The Gram-Schmidt passes
+// then read q_0..q_j from shared memory; global memory carries the SpMV
+// operand, the reduction partials and the per-unit scalars.  Steps, their
+// order, the per-thread accumulation order and the reductions are those of
+// the streaming kernels above, so both modes give the same numbers.
+// Shared layout: JacShared | coefficients | w of the tile | Q[k * trs + rl].
+// ----------------------------------------------------------------------------
+__host__ __device__ constexpr size_t res_align(size_t b) { return (b + 15) & ~(size_t)15; }
+
+template <typename V>
+__host__ __device__ constexpr size_t res_smem_bytes(int M, int trs) {
+  return res_align(sizeof(JacShared<V>)) + res_align(2 * sizeof(double) * RSB_MAXC) +
+         res_align(sizeof(V) * (size_t)trs) + sizeof(V) * (size_t)M * (size_t)trs;
+}
+
+// Dots of [1, D, q_0..] with the tile's w: the coefficient split across warps
+// and the per-lane row order of tile_dots.
+template <typename V>
+__device__ __forceinline__ void res_dots(const LzArgs<V>& a, const Tile& t, int nd, int nc,
+                                         const V* Qs, int trs, const V* ws,
+                                         Acc<V> (&acc)[MAXCW]) {
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nr = t.row1 - t.row0;
+#pragma unroll
+  for (int i = 0; i < MAXCW; ++i) {
+    const int c = w + RSB_WARPS * i;
+    if (c < nc) {
+      if (c == 0) {
+        for (int rl = lane; rl < nr; rl += 32) acc[i].add(V(1) * ws[rl]);
+      } else if (c <= nd) {
+        const double* d = c == 1 ? a.D0 : a.D1;
+        for (int rl = lane; rl < nr; rl += 32) acc[i].add(V(d[t.row0 + rl]) * ws[rl]);
+      } else {
+        const V* q = Qs + (size_t)(c - 1 - nd) * trs;
+        for (int rl = lane; rl < nr; rl += 32) acc[i].add(q[rl] * ws[rl]);
+      }
+    }
+  }
+}
+
+// w -= [1/sqrt(n), D, q_0..q_{nq-1}] cf, in the order of gs_update_rows.
+template <typename V>
+__device__ __forceinline__ V res_upd_row(const LzArgs<V>& a, const Unit& u, const double* cf,
+                                         int nd, int nq, const V* Qs, int trs, int rl, int r,
+                                         V w) {
+  if (unit_has(u, a.ckey, r)) w -= V(cf[0] * u.isn);
+  for (int l = 0; l < nd; ++l) w -= V(cf[1 + l]) * V((l == 0 ? a.D0 : a.D1)[r]);
+  const double* cq = cf + 1 + nd;
+  for (int k = 0; k < nq; ++k) w -= V(cq[k]) * Qs[(size_t)k * trs + rl];
+  return w;
+}
+
+template <typename V>
+__device__ __forceinline__ void res_store_dots(double* P, long long stride, int nc,
+                                               Acc<V> (&acc)[MAXCW], int tix) {
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+  for (int i = 0; i < MAXCW; ++i) {
+    const int c = w + RSB_WARPS * i;
+    if (c < nc) {
+      const double s = warp_sum(acc[i].get());
+      if (lane == 0) P[(long long)c * stride + tix] = s;
+    }
+  }
+}
+
+// The step phases write per-tile partials into P; after the grid barrier
+// every CTA of the unit reduces them itself (fixed order, so all CTAs hold
+// the same coefficients), which takes the last-CTA ticket and the staging of
+// the coefficients off the critical path.  Consecutive phases alternate
+// between two partial buffers: a buffer is rewritten only after a barrier
+// that follows every CTA's reduction of its previous contents.
+//
+// A(j): q_j = src * sc into shared memory, w = L q_j, dots [1, D, q_0..q_j]^T w.
+template <typename V>
+__device__ void res_a(const LzArgs<V>& a, int j, double sc, int tix, const Tile& t,
+                      const Unit& u, V* Qs, int trs, V* ws, double* P) {
+  const int nr = t.row1 - t.row0;
+  const V* src = (j & 1) ? a.W1 : a.W0;
+  const V s = V(sc);
+  const int nd = u.nd;
+  const int nc = 2 + nd + j;
+  unsigned long long pbytes = 0;
+  for (int rl = threadIdx.x; rl < nr; rl += RSB_BLOCK) {
+    const int r = t.row0 + rl;
+    const V xr = __ldcg(src + r);
+    ws[rl] = s * spmv_row<V, true>(a.slice_ptr, a.ent, src, r, xr);
+    Qs[(size_t)j * trs + rl] = s * xr;
+    if (a.pb_a)
+      pbytes += 4ull * row_width(a.slice_ptr, r) + sizeof(V) * (unsigned long long)(4 + j) +
+                8ull * nd;
+  }
+  __syncthreads();
+  Acc<V> acc[MAXCW];
+  res_dots<V>(a, t, nd, nc, Qs, trs, ws, acc);
+  res_store_dots<V>(P, a.stride, nc, acc, tix);
+  if (a.pb_a) prof_add(a.pb_a, pbytes);
+}
+
+// B(j): w -= basis c1, dots of the result (second pass).
+template <typename V>
+__device__ void res_b(const LzArgs<V>& a, int j, int tix, const Tile& t, const Unit& u,
+                      const V* Qs, int trs, V* ws, const double* c1, double* P) {
+  const int nr = t.row1 - t.row0;
+  const int nd = u.nd;
+  const int nc = 2 + nd + j;
+  unsigned long long pbytes = 0;
+  for (int rl = threadIdx.x; rl < nr; rl += RSB_BLOCK) {
+    const int r = t.row0 + rl;
+    ws[rl] = res_upd_row<V>(a, u, c1, nd, j + 1, Qs, trs, rl, r, ws[rl]);
+    if (a.pb_b) pbytes += sizeof(V) * (unsigned long long)(3 + j) + 8ull * nd;
+  }
+  __syncthreads();
+  Acc<V> acc[MAXCW];
+  res_dots<V>(a, t, nd, nc, Qs, trs, ws, acc);
+  res_store_dots<V>(P, a.stride, nc, acc, tix);
+  if (a.pb_b) prof_add(a.pb_b, pbytes);
+}
+
+// C(j): w -= basis c2 into W[(j + 1) & 1] (the next SpMV operand), ||w||^2.
+template <typename V>
+__device__ void res_c(const LzArgs<V>& a, int j, int tix, const Tile& t, const Unit& u,
+                      const V* Qs, int trs, const V* ws, const double* c2, double* sm,
+                      double* P) {
+  const int nr = t.row1 - t.row0;
+  const int nd = u.nd;
+  V* dst = (j & 1) ? a.W0 : a.W1;
+  Acc<V> acc;
+  unsigned long long pbytes = 0;
+  for (int rl = threadIdx.x; rl < nr; rl += RSB_BLOCK) {
+    const int r = t.row0 + rl;
+    const V w = res_upd_row<V>(a, u, c2, nd, j + 1, Qs, trs, rl, r, ws[rl]);
+    dst[r] = w;
+    acc.add(w * w);
+    if (a.pb_c) pbytes += sizeof(V) * (unsigned long long)(3 + j) + 8ull * nd;
+  }
+  if (a.pb_c) prof_add(a.pb_c, pbytes);
+  const double sum = block_sum(acc.get(), sm);
+  if (threadIdx.x == 0) P[tix] = sum;
+}
+
+// coefficients of a finished reduction: c[0] carries the 1/sqrt(n) of u0
+__device__ __forceinline__ void res_coef(const double* out, int nc, double isn, double* c) {
+  for (int k = threadIdx.x; k < nc; k += RSB_BLOCK) c[k] = k == 0 ? out[0] * isn : out[k];
+  __syncthreads();
+}
+
+// Ritz vector y = Q s_0 into Y and the kept vectors q_i <- Q s_i (i < kk) in
+// shared memory; the residual direction moves to W[kk & 1].
+template <typename V>
+__device__ void res_ritz(const LzArgs<V>& a, const Tile& t, const Unit& u, V* Qs, int trs,
+                         V* Ys) {
+  if (ldc<true>(&u.status) != U_ACTIVE) return;
+  const int nr = t.row1 - t.row0;
+  const int K = ldc<true>(&u.msteps);
+  const int kk = ldc<true>(&u.kk);
+  const double* Ym = unit_S(a.S, t.unit) + RSB_MAXM * RSB_MAXM;
+  constexpr int YS = RSB_MAXKEEP + 1;
+  for (int idx = threadIdx.x; idx < K * (kk + 1); idx += RSB_BLOCK) {
+    const int l = idx / (kk + 1), i = idx % (kk + 1);
+    Ys[l * YS + i] = V(__ldcg(Ym + l * RSB_MAXM + i));
+  }
+  __syncthreads();
+  const V* wl = (K & 1) ? a.W1 : a.W0;
+  V* wn = (kk & 1) ? a.W1 : a.W0;
+  for (int rl = threadIdx.x; rl < nr; rl += RSB_BLOCK) {
+    const int r = t.row0 + rl;
+    V q[RSB_MAXM];
+#pragma unroll
+    for (int l = 0; l < RSB_MAXM; ++l) q[l] = l < K ? Qs[(size_t)l * trs + rl] : V(0);
+    for (int i = 0; i <= kk; ++i) {
+      V acc = V(0);
+#pragma unroll
+      for (int l = 0; l < RSB_MAXM; ++l)
+        if (l < K) acc += Ys[l * YS + i] * q[l];
+      if (i == 0) a.Y[r] = acc;
+      if (i < kk) Qs[(size_t)i * trs + rl] = acc;
+    }
+    if (kk > 0 && wn != wl) wn[r] = __ldcg(wl + r);
+  }
+  if (a.pb_a && threadIdx.x == 0)
+    atomicAdd(a.pb_a, (unsigned long long)nr * sizeof(V) * (K + kk + 1));
+}
+
+template <typename V>
+__global__ void __launch_bounds__(RSB_BLOCK, 2)
+    k_lz_res(LzArgs<V> a, int M, int trs, double breakdown, int nunits, int maxcyc, GridBar* gb) {
+  extern __shared__ __align__(16) unsigned char res_sh[];
+  JacShared<V>& J = *reinterpret_cast<JacShared<V>*>(res_sh);
+  size_t off = res_align(sizeof(JacShared<V>));
+  double* c1 = reinterpret_cast<double*>(res_sh + off);
+  double* c2 = c1 + RSB_MAXC;
+  off += res_align(2 * sizeof(double) * RSB_MAXC);
+  V* ws = reinterpret_cast<V*>(res_sh + off);
+  off += res_align(sizeof(V) * (size_t)trs);
+  V* Qs = reinterpret_cast<V*>(res_sh + off);
+  __shared__ double out[RSB_MAXC];
+  __shared__ double sm[RSB_WARPS];
+  const unsigned G = gridDim.x;
+  const int tix = blockIdx.x;
+  const Tile t = a.tiles[tix];
+  Unit& u = a.units[t.unit];
+  const bool lead = tix == u.tile0 && threadIdx.x == 0;
+  double* const Pb[2] = {a.partials, a.partials + (long long)RSB_MAXC * a.stride};
+  int* jm = a.jmin;  // two slots: read one at a cycle's start, refill the other
+  for (int cyc = 0; cyc < maxcyc; ++cyc) {
+    const int jstart = cyc == 0 ? 0 : min(max(__ldcg(jm + (cyc & 1)), 0), M);
+    if (tix == 0 && threadIdx.x == 0) jm[(cyc + 1) & 1] = 0x7FFFFFFF;
+    LzArgs<V> ac = a;
+    ac.jmin = jm + ((cyc + 1) & 1);
+    // the unit's step state, tracked identically by all of its CTAs
+    const bool on = __ldcg(&u.status) == U_ACTIVE;
+    const int j0 = __ldcg(&u.j0);
+    int msteps = __ldcg(&u.msteps);
+    double beta = __ldcg(&u.beta0);
+    const int nd = u.nd;
+    int ph = 0;
+    for (int j = jstart; j < M; ++j) {
+      const bool st = on && j < msteps && j >= j0;
+      const int nc = 2 + nd + j;
+      if (st) res_a<V>(a, j, 1.0 / beta, tix, t, u, Qs, trs, ws, Pb[ph & 1]);
+      if (!grid_sync(gb, G)) return;
+      if (st) {
+        final_reduce(Pb[ph & 1], a.stride, u.tile0, u.ntile, nc, out);
+        res_coef(out, nc, u.isn, c1);
+        res_b<V>(a, j, tix, t, u, Qs, trs, ws, c1, Pb[(ph + 1) & 1]);
+      }
+      if (!grid_sync(gb, G)) return;
+      if (st) {
+        final_reduce(Pb[(ph + 1) & 1], a.stride, u.tile0, u.ntile, nc, out);
+        res_coef(out, nc, u.isn, c2);
+        if (tix == u.tile0) {  // column j of S = Q^T L Q
+          double* Sm = unit_S(a.S, t.unit);
+          for (int k = threadIdx.x; k <= j; k += RSB_BLOCK) {
+            const double v = c1[1 + nd + k] + c2[1 + nd + k];
+            Sm[k * RSB_MAXM + j] = v;
+            Sm[j * RSB_MAXM + k] = v;
+          }
+        }
+        res_c<V>(a, j, tix, t, u, Qs, trs, ws, c2, sm, Pb[ph & 1]);
+      }
+      if (!grid_sync(gb, G)) return;
+      if (st) {
+        final_reduce(Pb[ph & 1], a.stride, u.tile0, u.ntile, 1, out);
+        beta = sqrt(out[0]);
+        if (lead) u.beta[j + 1] = beta;
+        if (beta <= breakdown * u.dmax) {  // invariant subspace: the cycle ends here
+          msteps = j + 1;
+          if (lead) {
+            u.msteps = j + 1;
+            u.broke = 1;
+          }
+        }
+      }
+      ++ph;
+    }
+    for (int uu = blockIdx.x; uu < nunits; uu += G) lz_eig_u<V, true>(a.units[uu], unit_S(a.S, uu), J);
+    if (!grid_sync(gb, G)) return;
+    res_ritz<V>(a, t, u, Qs, trs, &J.Z[0][0]);
+    if (!grid_sync(gb, G)) return;
+    lz_resid_t<V, true>(ac, a.Y, 0, tix, sm, out);
+    if (!grid_sync(gb, G)) return;
+    proj2_t<V, true>(a, a.Y, tix, sm, out);
+    if (!grid_sync(gb, G)) return;
+    proj3_t<V, true>(a, a.Y, tix, sm, out);
+    if (!grid_sync(gb, G)) return;
+    if (__ldcg(a.n_active) == 0) break;
+  }
+}
+
 // Start vector into Y: hash of gid on unit rows (or a given vector), 0 elsewhere.
 template <typename V>
 __global__ void __launch_bounds__(RSB_BLOCK) k_start(LzArgs<V> a, uint64_t sd, const double* from64,
@@ -865,6 +1146,7 @@ static LzArgs<V> make_args(const LevelGraph& G, const Tile* tiles, int ntiles, U
 
 int solver_setup(Unit* units, int nunits, int nd, int krylov, int maxcycles, double tol,
                  int require_cluster, int keep, SolveBufs& B, cudaStream_t s) {
+  B.maxcycles = maxcycles;
   RSB_CK(cudaMemsetAsync(B.n_active, 0, sizeof(int), s));
   k_solve_init<<<(nunits + 127) / 128, 128, 0, s>>>(units, nunits, nd, krylov, maxcycles, tol,
                                                     require_cluster, keep, B.n_active);
@@ -940,6 +1222,35 @@ static int lanczos_run(const LevelGraph& G, const Tile* tiles, int ntiles, Unit*
   rc = lz_start<V>(a, ntiles, sd, from64, from32, s);
   if (rc) return rc;
   const double breakdown = 1e-14;
+  if (use_graph == 3 && B.gb && B.trmax > 0) {
+    // the whole solve in one cooperative launch when every tile gets a
+    // co-resident CTA holding its rows of the basis; otherwise CUDA graphs
+    int dev = 0, nsm = 0, optin = 0, occ = 0;
+    RSB_CK(cudaGetDevice(&dev));
+    RSB_CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    RSB_CK(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    int trs = B.trmax;
+    const size_t smem = res_smem_bytes<V>(M, trs);
+    if (smem + 1024 <= (size_t)optin) {  // room for the kernel's static shared memory
+      RSB_CK(cudaFuncSetAttribute(k_lz_res<V>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)smem));
+      RSB_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_lz_res<V>, RSB_BLOCK, smem));
+      if ((long long)occ * nsm >= ntiles) {
+        int maxcyc = B.maxcycles + 1;
+        double bd = breakdown;
+        GridBar* gb = B.gb;
+        void* args[] = {(void*)&a, (void*)&M, (void*)&trs, (void*)&bd, (void*)&nunits,
+                        (void*)&maxcyc, (void*)&gb};
+        const int pi = prof_before(PROF_CYCLE, s);
+        cudaError_t e = cudaLaunchCooperativeKernel((const void*)k_lz_res<V>, ntiles, RSB_BLOCK,
+                                                    args, smem, s);
+        rsb_count_launch(1);
+        if (e != cudaSuccess) return rsb_set_cuda_error(e, "cudaLaunchCooperativeKernel(k_lz_res)");
+        prof_after(pi, s);
+        return read_active(B, s, &active);
+      }
+    }
+  }
   if (use_graph == 2 && B.gb) {
     // one persistent cooperative launch per cycle
     int dev = 0, nsm = 0, occ = 0;

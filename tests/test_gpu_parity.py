@@ -107,6 +107,19 @@ def test_fiedler_mixed_polish_reaches_fp64(cycles, dim):
     assert res <= 1e-9 * O.degree(g).max()
 
 
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("dims", [(64, 64, 32), (25, 22, 12), (128, 128, 96)])
+def test_resident_launch_matches_graph_launch_bit_for_bit(precision, dims):
+    # launch mode 3 keeps each tile's basis rows in shared memory when the level
+    # fits (the first two), else falls back to graphs (the third); the steps and
+    # their accumulation order are those of the streaming kernels
+    G = R.graph(box_graph(*dims))
+    ref = R.rsb_fiedler(G, R.options(precision=precision, use_graph=1))
+    res = R.rsb_fiedler(G, R.options(precision=precision, use_graph=3))
+    assert ref[0] == res[0] and ref[2] == res[2] and ref[3] == res[3]
+    assert torch.equal(ref[1], res[1])
+
+
 def test_mixed_partition_resolves_tied_slab_like_oracle():
     # 9x24x13 -> 16: after the 24-axis split the 13-axis median falls inside the
     # middle slab, whose values tie (cos = 0); the tie must go by gid (R7) as in
@@ -167,7 +180,7 @@ def _closed_c1():
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
 @pytest.mark.parametrize("batched", [1, 0])
-@pytest.mark.parametrize("use_graph", [2, 1, 0])
+@pytest.mark.parametrize("use_graph", [3, 2, 1, 0])
 def test_partition_c1_closed_form(precision, batched, use_graph):
     g = box_graph(16, 8, 4)
     part, st, code = R.rsb_partition(R.graph(g), 8, R.options(precision=precision, batched=batched,
@@ -299,7 +312,7 @@ def _closed_c2():
 
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
-@pytest.mark.parametrize("use_graph", [2, 1])
+@pytest.mark.parametrize("use_graph", [3, 2, 1])
 def test_partition_c2_closed_form(precision, use_graph):
     g = box_graph(64, 64, 32)
     part, st, code = R.rsb_partition(R.graph(g), 64, R.options(precision=precision,
