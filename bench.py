@@ -3,11 +3,13 @@
 Default workload: the 64x64x32 box hex mesh (131,072 elements), face-adjacency
 dual graph with unit weights, bisected to 64 parts (6 levels) by Lanczos in
 mixed precision (FP32 vectors, FP64 coefficients / tridiagonal / Rayleigh
-quotient), every level's subgraphs batched in one set of launches, each
-Lanczos cycle replayed as one CUDA graph (--launch 2: one persistent
-cooperative kernel per cycle).  A step is one full rsb_partition call from
-device-resident CSR to part ids.  metric = (sum over levels and split
-segments of their element count) / time.
+quotient), every level's subgraphs batched in one set of launches; the tile
+rows and the launch mode (3: one persistent cooperative kernel per solve with
+the basis in shared memory when the level fits; 1: one CUDA graph per cycle)
+are picked by rsb_autotune before the timed region (--launch fixes the mode
+instead).  A step is one full rsb_partition call from device-resident CSR to
+part ids.  metric = (sum over levels and split segments of their element
+count) / time.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
@@ -197,6 +199,13 @@ def aggregate(total_ms: float, units: float, dist=None, device=None):
 # ----------------------------------------------------------------------------
 # our arm
 # ----------------------------------------------------------------------------
+LAUNCH_NAMES = ["kernels", "cuda_graph", "persistent_cycle", "persistent_resident"]
+KERNEL_NAMES = {
+    ("cycle", 3): ("k_lz_res (one cooperative launch per Fiedler solve: SpMV, CGS2 against the "
+                   "shared-memory-resident basis, Jacobi Ritz pairs, thick restart; FP32 stage "
+                   "and FP64 polish)"),
+    ("cycle", 2): "k_lz_cycle (one cooperative launch per Lanczos cycle)",
+}
 WORKLOAD_NAME = ("box 64x64x32 hex mesh, face-adjacency dual graph, unit weights, "
                  "131072 elements -> 64 parts (6 levels)")
 
@@ -221,9 +230,15 @@ def our_arm(args):
     P = W["parts"]
     G = R.graph(g, device=f"cuda:{local}")
     opts = R.options(method=W["method"], precision=args.precision, degenerate_policy=W["degenerate"],
-                     batched=1, use_graph=args.launch)
+                     batched=1, use_graph=args.launch if args.launch is not None else 3)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=f"cuda:{local}")
     out = torch.empty(g.n, dtype=torch.int32, device=f"cuda:{local}")
+    tuned = None
+    if args.launch is None:  # autotuned tile rows and launch mode (before the timed region)
+        opts, tune_ms = R.rsb_autotune([G], [P], opts, outs=[out])
+        tuned = {"tile_rows": opts.tile_rows, "launch": LAUNCH_NAMES[opts.use_graph],
+                 "candidates_ms": {f"{t}x{LAUNCH_NAMES[l]}": round(v, 3)
+                                   for (t, l), v in tune_ms.items()}}
 
     def step():
         return R.rsb_partition(G, P, opts, out=out, allow_noconv=True)
@@ -232,7 +247,8 @@ def our_arm(args):
         step()
     torch.cuda.synchronize()
     # timed region: device-resident inputs, L2 flushed between steps
-    fam = args.profile
+    fam = args.profile if args.profile != "auto" else ("cycle" if opts.use_graph in (2, 3)
+                                                        else "lz_b")
     clocks = Clocks(local)
     ms_steps, units, launches = [], 0, 0
     if dist is not None:
@@ -302,7 +318,7 @@ def our_arm(args):
         for name, kw in (("fp64_batched", dict(precision="fp64", batched=1)),
                          ("fp64_plain", dict(precision="fp64", batched=0))):
             o2 = R.options(method=W["method"], degenerate_policy=W["degenerate"],
-                           use_graph=args.launch, **kw)
+                           use_graph=opts.use_graph, tile_rows=opts.tile_rows, **kw)
             R.rsb_partition(G, P, o2, out=out)
             torch.cuda.synchronize()
             e0 = torch.cuda.Event(enable_timing=True)
@@ -333,15 +349,15 @@ def our_arm(args):
         "dtype": "f32/f64" if args.precision == "mixed" else "f64",
         "data": "synthetic",
         "config": {"workload": WORKLOAD_NAME, "method": W["method"], "precision": args.precision,
-                   "batched": True, "launch": ["kernels", "cuda_graph", "persistent"][args.launch], "elements": g.n, "parts": P,
+                   "batched": True, "launch": LAUNCH_NAMES[opts.use_graph],
+                   "tile_rows": opts.tile_rows, "autotune": tuned, "elements": g.n, "parts": P,
                    "l2": "flushed between steps (256 MiB write)", "matches_closed_form": ok},
         "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "gpu_launches": launches,
         "roofline": {"bound": "hbm",
-                     "kernel": ("k_lz_cycle<float> (persistent cooperative Lanczos cycle: SpMV, "
-                                "CGS2, tridiagonal, Ritz, residual, restart)") if fam == "cycle"
-                     else f"lanczos kernel family '{fam}'",
+                     "kernel": KERNEL_NAMES.get((fam, opts.use_graph),
+                                                f"lanczos kernel family '{fam}'"),
                      "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak if peak else None, "traffic": None,
                      "peak_kind": peak_kind, "launches_timed": prof_launches,
@@ -378,9 +394,12 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="c2", choices=sorted(WORKLOADS))
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
-    ap.add_argument("--profile", default="lz_b", choices=["cycle", "lz_a", "lz_b", "lz_c", "cg_ap"])
-    ap.add_argument("--launch", type=int, default=1, choices=[0, 1, 2],
-                    help="Lanczos cycle launch mode: 0 kernels, 1 CUDA graph, 2 persistent kernel")
+    ap.add_argument("--profile", default="auto",
+                    choices=["auto", "cycle", "lz_a", "lz_b", "lz_c", "cg_ap"])
+    ap.add_argument("--launch", type=int, default=None, choices=[0, 1, 2, 3],
+                    help="fix the Lanczos launch mode (0 kernels, 1 CUDA graph per cycle, "
+                         "2 persistent kernel per cycle, 3 resident persistent kernel per "
+                         "solve) instead of autotuning it with the tile rows")
     ap.add_argument("--quick", action="store_true", help="skip the FP64/SpMV/CPU extras")
     args = ap.parse_args()
     if args.impl == "reference":

@@ -121,7 +121,7 @@ typedef struct rsb_stats {
 
 /* Fills *o with the defaults: Lanczos, FP64, krylov_dim 40, max_restarts 50,
  * tol 1e-10, cg_tol 1e-12, cg_maxit 4000, max_outer 50, RESOLVE,
- * cluster_tol 0.05, tie_rel 1e-5, mixed_tol 1e-6, batched 1, use_graph 1,
+ * cluster_tol 0.05, tie_rel 1e-5, mixed_tol 1e-6, batched 1, use_graph 3,
  * validate 0, polish_cycles 2, keep 8, tile_rows 0, polish_dim 16. */
 void rsb_options_default(rsb_options *o);
 
@@ -165,6 +165,30 @@ int rsb_partition(const rsb_csr *g, int32_t nparts, const rsb_options *o,
 int rsb_partition_batch(const rsb_csr *gs, int32_t nmesh, const int32_t *nparts,
                         const rsb_options *o, int32_t *const *parts, rsb_stats *st,
                         void *stream);
+
+/*
+ * rsb_autotune: picks the tile rows (2, 4 or 8 rows per thread; a solver tile
+ * is 256 x that many rows of one subgraph) and the launch mode of the Lanczos
+ * cycles (3 or 1, see use_graph) for a workload by timing it.  Each of the
+ * RSB_TUNE_CANDIDATES candidates, in the order (2,3) (4,3) (8,3) (2,1) (4,1)
+ * (8,1) of (tile_rows, use_graph), runs one bisection level of the given meshes
+ * with two Lanczos cycles, no polish and no deflated candidates, once untimed
+ * and twice timed with CUDA events on the stream; the fastest is written into
+ * o->tile_rows and o->use_graph, every other field of *o is kept.  Launch
+ * modes give identical results; tile rows change the order of the reductions'
+ * partial sums (rounding only).
+ *   gs, nmesh, nparts, parts  as in rsb_partition_batch; parts[m] is
+ *           overwritten (scratch)
+ *   o       in: the options of the real run; out: with the chosen tile_rows
+ *           and use_graph (host pointer, not NULL)
+ *   ms_out  optional host array of RSB_TUNE_CANDIDATES doubles: the best time
+ *           of each candidate in ms
+ * The call synchronises the stream.  Returns the first error of a candidate
+ * run (RSB_ENOCONV of the two-cycle runs is expected and ignored).
+ */
+#define RSB_TUNE_CANDIDATES 6
+int rsb_autotune(const rsb_csr *gs, int32_t nmesh, const int32_t *nparts, rsb_options *o,
+                 int32_t *const *parts, double *ms_out, void *stream);
 
 /*
  * Fiedler pair of a connected graph (§4, Eqs. eigen0/eigen1; §6 or §7).

@@ -312,7 +312,7 @@ extern "C" void rsb_options_default(rsb_options* o) {
   o->tie_rel = 1e-5;
   o->mixed_tol = 1e-6;
   o->batched = 1;
-  o->use_graph = 1;
+  o->use_graph = 3;
   o->validate = 0;
   o->polish_cycles = 2;
   o->keep = 8;
@@ -1035,6 +1035,70 @@ extern "C" int rsb_partition(const rsb_csr* g, int32_t nparts, const rsb_options
   if (!g) return rsb_set_error(RSB_EINVAL, "NULL graph");
   int32_t* const parts[1] = {part};
   return rsb_partition_batch(g, 1, &nparts, o, parts, st, stream);
+}
+
+// ----------------------------------------------------------------------------
+// rsb_autotune: tile rows x launch mode, timed on the caller's workload
+// ----------------------------------------------------------------------------
+static const int kTuneTile[RSB_TUNE_CANDIDATES] = {2, 4, 8, 2, 4, 8};
+static const int kTuneLaunch[RSB_TUNE_CANDIDATES] = {3, 3, 3, 1, 1, 1};
+
+extern "C" int rsb_autotune(const rsb_csr* gs, int32_t nmesh, const int32_t* nparts,
+                            rsb_options* o, int32_t* const* parts, double* ms_out,
+                            void* stream) {
+  if (!gs || !nparts || !o || !parts || nmesh < 1) return rsb_set_error(RSB_EINVAL, "autotune args");
+  int rc = check_options(*o);
+  if (rc) return rc;
+  // one bisection level, two Lanczos cycles, no polish and no deflated
+  // candidates: the kernels and launches of a cycle, at the workload's size
+  std::vector<int32_t> np(nmesh);
+  for (int m = 0; m < nmesh; ++m) np[m] = std::min<int32_t>(nparts[m], 2);
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  RSB_CK(cudaEventCreate(&e0));
+  RSB_CK(cudaEventCreate(&e1));
+  double best = 1e300;
+  int pick = 0;
+  for (int c = 0; c < RSB_TUNE_CANDIDATES && rc == RSB_OK; ++c) {
+    rsb_options t = *o;
+    t.tile_rows = kTuneTile[c];
+    t.use_graph = kTuneLaunch[c];
+    t.max_restarts = 2;
+    t.tol = 1e-300;
+    t.mixed_tol = 1e-300;
+    t.polish_cycles = 0;
+    t.degenerate_policy = RSB_DEGEN_NONE;
+    t.method = RSB_LANCZOS;
+    double ms = 1e300;
+    for (int rep = 0; rep < 3 && rc == RSB_OK; ++rep) {  // first call warms up
+      cudaEventRecord(e0, s);
+      int r = rsb_partition_batch(gs, nmesh, np.data(), &t, parts, nullptr, stream);
+      cudaEventRecord(e1, s);
+      if (r != RSB_OK && r != RSB_ENOCONV) {
+        rc = r;
+        break;
+      }
+      cudaError_t ce = cudaEventSynchronize(e1);
+      if (ce != cudaSuccess) {
+        rc = rsb_set_cuda_error(ce, "autotune timing");
+        break;
+      }
+      float f = 0.f;
+      cudaEventElapsedTime(&f, e0, e1);
+      if (rep > 0) ms = std::min(ms, (double)f);
+    }
+    if (ms_out) ms_out[c] = ms;
+    if (rc == RSB_OK && ms < best) {
+      best = ms;
+      pick = c;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc) return rc;
+  o->tile_rows = kTuneTile[pick];
+  o->use_graph = kTuneLaunch[pick];
+  return RSB_OK;
 }
 
 // ----------------------------------------------------------------------------

@@ -221,15 +221,21 @@ __device__ __forceinline__ bool last_cta(unsigned int* cnt, int ntile) {
 }
 
 // Grid-wide barrier of a cooperative (co-resident) launch: generation counter,
-// thread 0 of each CTA arrives and waits.  The wait is bounded (about 10 s);
-// on timeout the error word is set and every CTA that reaches a barrier
-// afterwards returns false, so the kernel ends instead of hanging.
+// thread 0 of each CTA arrives and waits.  The wait is bounded (4 s of the
+// global timer); on timeout the error word is set and every CTA that reaches a
+// barrier afterwards returns false, so the kernel ends instead of hanging.
 struct GridBar {
   unsigned int count;
   unsigned int gen;
   int err;
   int pad;
 };
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
 
 __device__ __forceinline__ bool grid_sync(GridBar* b, unsigned nblocks) {
   __shared__ int s_ok;
@@ -245,14 +251,16 @@ __device__ __forceinline__ bool grid_sync(GridBar* b, unsigned nblocks) {
       __threadfence();
       atomicAdd(&b->gen, 1u);
     } else {
-      long long spins = 0;
+      const unsigned long long t0 = global_ns();
+      unsigned spins = 0;
       while (*vgen == g) {
         if (*verr) break;
-        if (++spins > (1ll << 27)) {
+        ++spins;
+        if ((spins & 255u) == 0 && global_ns() - t0 > 4000000000ull) {
           atomicExch(&b->err, 1);
           break;
         }
-        __nanosleep(64);
+        if (spins > 32) __nanosleep(32);
       }
     }
     __threadfence();

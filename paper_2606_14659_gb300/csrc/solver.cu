@@ -414,6 +414,9 @@ struct JacShared {
 // T = double for the FP64 path; T = float for the mixed path, whose Lanczos
 // vectors are FP32 (so FP32-accurate Ritz vectors lose nothing) and whose
 // eigenvalue comes from the FP64 Rayleigh quotient at the end.
+// tasks per thread and round: np*np + np*n2 <= 20*20 + 20*40 over RSB_BLOCK threads
+#define EIG_TASKS ((RSB_MAXM * RSB_MAXM * 3 / 4 + RSB_BLOCK - 1) / RSB_BLOCK)
+
 template <typename T, bool CO>
 __device__ void lz_eig_u(Unit& u, double* Sm, JacShared<T>& J) {
   if (ldc<CO>(&u.status) != U_ACTIVE) return;
@@ -438,6 +441,24 @@ __device__ void lz_eig_u(Unit& u, double* Sm, JacShared<T>& J) {
   __syncthreads();
   const double eps2 = sizeof(T) == 8 ? 1e-30 : 1e-14;
   const double thr = fro * eps2;
+  // this thread's tasks of every round: np*np blocks of A (pair i1 x pair i2),
+  // then np*n2 (pair, row) updates of Z; fixed for the whole solve
+  const int np = n2 / 2;
+  int ta[EIG_TASKS], tb[EIG_TASKS];
+#pragma unroll
+  for (int k = 0; k < EIG_TASKS; ++k) {
+    const int task = tid + k * RSB_BLOCK;
+    ta[k] = -1;
+    tb[k] = 0;
+    if (task < np * np) {
+      ta[k] = task / np;
+      tb[k] = task - ta[k] * np;
+    } else if (task < np * np + np * n2) {
+      const int zt = task - np * np;
+      ta[k] = -2;
+      tb[k] = ((zt / n2) << 8) | (zt % n2);
+    }
+  }
   for (int sweep = 0; sweep < 20; ++sweep) {
     double off = 0.0;
     for (int idx = tid; idx < K * K; idx += RSB_BLOCK) {
@@ -450,18 +471,20 @@ __device__ void lz_eig_u(Unit& u, double* Sm, JacShared<T>& J) {
     off = J.red[0];
     __syncthreads();
     if (off <= thr) break;
-    const int np = n2 / 2;
     for (int rnd = 0; rnd < n2 - 1; ++rnd) {
       if (tid < np) {
-        int pa = tid == 0 ? 0 : ((tid + rnd - 1) % (n2 - 1)) + 1;
-        int pb = ((n2 - 1 - tid + rnd - 1) % (n2 - 1)) + 1;
+        // round-robin pairing: slot 0 holds index 0, the others rotate
+        int ia = tid + rnd - 1, ib = n2 - 2 - tid + rnd;
+        if (ia >= n2 - 1) ia -= n2 - 1;
+        if (ib >= n2 - 1) ib -= n2 - 1;
+        int pa = tid == 0 ? 0 : ia + 1;
+        int pb = ib + 1;
         if (pa > pb) { const int tt = pa; pa = pb; pb = tt; }
         T cc = T(1), ss = T(0);
         const T apq = J.A[pa][pb];
         if (pb < K && apq != T(0)) {
           const T tau = (J.A[pb][pb] - J.A[pa][pa]) / (T(2) * apq);
-          const T tt = tau >= T(0) ? T(1) / (tau + sqrt(T(1) + tau * tau))
-                                   : T(-1) / (-tau + sqrt(T(1) + tau * tau));
+          const T tt = (tau >= T(0) ? T(1) : T(-1)) / (fabs(tau) + sqrt(T(1) + tau * tau));
           cc = T(1) / sqrt(T(1) + tt * tt);
           ss = tt * cc;
         }
@@ -474,9 +497,10 @@ __device__ void lz_eig_u(Unit& u, double* Sm, JacShared<T>& J) {
       // the round's rotations act on disjoint index pairs, so every 2x2 block
       // (pair i1 rows, pair i2 columns) is updated in place by one thread:
       // the column rotation, then the row rotation; Z takes the column one
-      for (int task = tid; task < np * np + np * n2; task += RSB_BLOCK) {
-        if (task < np * np) {
-          const int i1 = task / np, i2 = task - i1 * np;
+#pragma unroll
+      for (int k = 0; k < EIG_TASKS; ++k) {
+        if (ta[k] >= 0) {
+          const int i1 = ta[k], i2 = tb[k];
           const int p1 = J.p[i1], q1 = J.q[i1], p2 = J.p[i2], q2 = J.q[i2];
           const T c1 = J.c[i1], s1 = J.s[i1], c2 = J.c[i2], s2 = J.s[i2];
           const T a11 = J.A[p1][p2], a12 = J.A[p1][q2], a21 = J.A[q1][p2], a22 = J.A[q1][q2];
@@ -486,9 +510,8 @@ __device__ void lz_eig_u(Unit& u, double* Sm, JacShared<T>& J) {
           J.A[q1][p2] = s1 * b11 + c1 * b21;
           J.A[p1][q2] = c1 * b12 - s1 * b22;
           J.A[q1][q2] = s1 * b12 + c1 * b22;
-        } else {
-          const int zt = task - np * np;
-          const int i = zt / n2, r = zt - i * n2;
+        } else if (ta[k] == -2) {
+          const int i = tb[k] >> 8, r = tb[k] & 255;
           const int pa = J.p[i], pb = J.q[i];
           const T cc = J.c[i], ss = J.s[i];
           const T zx = J.Z[r][pa], zy = J.Z[r][pb];

@@ -24,7 +24,10 @@ RSB_DEGEN_NONE, RSB_DEGEN_RESOLVE = 0, 1
 EXPORTED = ["rsb_options_default", "rsb_partition", "rsb_partition_batch", "rsb_fiedler",
             "rsb_laplacian_apply", "rsb_laplacian_apply_f32", "rsb_laplacian_bench",
             "rsb_strerror", "rsb_last_error_detail", "rsb_release", "rsb_profile_begin",
-            "rsb_profile_end", "rsb_laplacian_apply_noalloc"]
+            "rsb_profile_end", "rsb_laplacian_apply_noalloc", "rsb_autotune"]
+
+RSB_TUNE_CANDIDATES = 6
+TUNE_CANDIDATES = [(2, 3), (4, 3), (8, 3), (2, 1), (4, 1), (8, 1)]  # (tile_rows, use_graph)
 
 
 class rsb_csr(C.Structure):
@@ -79,6 +82,8 @@ def load():
     lib.rsb_laplacian_apply_noalloc.argtypes = [C.POINTER(rsb_csr), vp, vp, vp]
     lib.rsb_laplacian_bench.argtypes = [C.POINTER(rsb_csr), C.c_int, C.c_int,
                                         C.POINTER(C.c_double), C.POINTER(C.c_double), vp]
+    lib.rsb_autotune.argtypes = [C.POINTER(rsb_csr), C.c_int32, C.POINTER(C.c_int32),
+                                 C.POINTER(rsb_options), C.POINTER(vp), C.POINTER(C.c_double), vp]
     lib.rsb_strerror.argtypes = [C.c_int]
     lib.rsb_strerror.restype = C.c_char_p
     lib.rsb_last_error_detail.argtypes = []
@@ -90,7 +95,8 @@ def load():
     lib.rsb_profile_end.argtypes = [C.POINTER(C.c_double), C.POINTER(C.c_int64),
                                     C.POINTER(C.c_double)]
     lib.rsb_profile_end.restype = None
-    for name in ("rsb_partition", "rsb_partition_batch", "rsb_fiedler", "rsb_laplacian_apply",
+    for name in ("rsb_partition", "rsb_partition_batch", "rsb_fiedler", "rsb_autotune",
+                 "rsb_laplacian_apply",
                  "rsb_laplacian_apply_f32", "rsb_laplacian_bench", "rsb_laplacian_apply_noalloc"):
         getattr(lib, name).restype = C.c_int
     _lib = lib
@@ -237,6 +243,28 @@ def rsb_partition_batch(gs: list, nparts: list, opts: rsb_options | None = None,
     code = lib.rsb_partition_batch(arr, m, np_, C.byref(o), ptrs, C.byref(st), _stream(stream))
     _check(code, "rsb_partition_batch", (RSB_OK, RSB_ENOCONV) if allow_noconv else (RSB_OK,))
     return outs, st.as_dict(), code
+
+
+def rsb_autotune(gs: list, nparts: list, opts: rsb_options | None = None, outs=None,
+                 stream=None):
+    """Times the tile-rows x launch-mode candidates on one bisection level of the
+    given meshes.  Returns (options with the chosen tile_rows and use_graph,
+    {(tile_rows, use_graph): ms})."""
+    lib = load()
+    import torch
+
+    m = len(gs)
+    if outs is None:
+        outs = [torch.empty(g.n, dtype=torch.int32, device=g.device) for g in gs]
+    arr = (rsb_csr * m)(*[g.c_struct() for g in gs])
+    np_ = (C.c_int32 * m)(*[int(p) for p in nparts])
+    ptrs = (C.c_void_p * m)(*[_ptr(o) for o in outs])
+    o = rsb_options()
+    C.memmove(C.byref(o), C.byref(opts if opts is not None else options()), C.sizeof(o))
+    ms = (C.c_double * RSB_TUNE_CANDIDATES)()
+    code = lib.rsb_autotune(arr, m, np_, C.byref(o), ptrs, ms, _stream(stream))
+    _check(code, "rsb_autotune")
+    return o, {c: ms[i] for i, c in enumerate(TUNE_CANDIDATES)}
 
 
 def rsb_fiedler(g: Graph, opts: rsb_options | None = None, out=None, stream=None):

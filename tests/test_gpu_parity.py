@@ -108,14 +108,16 @@ def test_fiedler_mixed_polish_reaches_fp64(cycles, dim):
 
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
-@pytest.mark.parametrize("dims", [(64, 64, 32), (25, 22, 12), (128, 128, 96)])
-def test_resident_launch_matches_graph_launch_bit_for_bit(precision, dims):
+@pytest.mark.parametrize("dims,tile_rows", [((64, 64, 32), 2), ((64, 64, 32), 4),
+                                            ((25, 22, 12), 2), ((128, 128, 96), 2)])
+def test_resident_launch_matches_graph_launch_bit_for_bit(precision, dims, tile_rows):
     # launch mode 3 keeps each tile's basis rows in shared memory when the level
-    # fits (the first two), else falls back to graphs (the third); the steps and
-    # their accumulation order are those of the streaming kernels
+    # fits (the 64x64x32 and 25x22x12 boxes), else falls back to graphs (the
+    # 128x128x96 box); the steps and their accumulation order are those of the
+    # streaming kernels
     G = R.graph(box_graph(*dims))
-    ref = R.rsb_fiedler(G, R.options(precision=precision, use_graph=1))
-    res = R.rsb_fiedler(G, R.options(precision=precision, use_graph=3))
+    ref = R.rsb_fiedler(G, R.options(precision=precision, use_graph=1, tile_rows=tile_rows))
+    res = R.rsb_fiedler(G, R.options(precision=precision, use_graph=3, tile_rows=tile_rows))
     assert ref[0] == res[0] and ref[2] == res[2] and ref[3] == res[3]
     assert torch.equal(ref[1], res[1])
 
@@ -320,3 +322,18 @@ def test_partition_c2_closed_form(precision, use_graph):
     assert np.array_equal(_np(part), _closed_c2())
     assert st["levels"] == 6
     assert abs(st["lambda_first"] - O.box_lambda2(64, 64, 32)) <= 1e-6 * O.box_lambda2(64, 64, 32)
+
+
+def test_autotune_picks_a_candidate_and_keeps_results():
+    g = box_graph(64, 64, 32)
+    G = R.graph(g)
+    base = R.options(precision="mixed")
+    tuned, ms = R.rsb_autotune([G], [64], base)
+    assert (tuned.tile_rows, tuned.use_graph) in ms
+    assert all(np.isfinite(v) and v > 0 for v in ms.values())
+    assert ms[(tuned.tile_rows, tuned.use_graph)] == min(ms.values())
+    for f, _ in R.rsb.rsb_options._fields_:
+        if f not in ("tile_rows", "use_graph"):
+            assert getattr(tuned, f) == getattr(base, f), f
+    part, st, code = R.rsb_partition(G, 64, tuned)
+    assert code == 0 and np.array_equal(_np(part), _closed_c2())
