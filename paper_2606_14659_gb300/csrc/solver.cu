@@ -7,10 +7,14 @@
 //   B: w -= basis * c1, fused with the second pass's dot products,
 //   C: w -= basis * c2, fused with ||w||^2 -> beta_{j+1}.
 // q_{j+1} = w / beta_{j+1} is materialised by the next step's A, which gathers
-// the unnormalised w and scales.  After the cycle: the smallest eigenpair of
-// the tridiagonal T (one warp per unit, FP64), the Ritz vector y = Q t, the
-// true residual ||L y - theta y||, and an explicit restart from y projected
-// against the fixed basis (two classical Gram-Schmidt passes).
+// the unnormalised w and scales.  After the cycle: the Ritz pairs of the
+// projected matrix S = Q^T L Q (parallel cyclic Jacobi, one CTA per unit), the
+// Ritz vector y = Q t, the true residual ||L y - theta y||, and a thick restart
+// from the kept Ritz vectors and the last residual direction (an explicit
+// restart from y, projected against the fixed basis, when a cycle ended on an
+// invariant subspace).  Launch modes: one kernel per step phase (optionally
+// replayed as a CUDA graph per cycle), one cooperative kernel per cycle, or one
+// cooperative kernel per solve with the basis resident in shared memory.
 //
 // Inverse iteration (paper §7, Algorithm 2): the right-hand side b is the
 // projected, normalised previous iterate; L x = b is solved by CG from x0 = 0
