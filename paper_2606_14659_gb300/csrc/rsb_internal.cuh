@@ -202,6 +202,55 @@ template <> struct Acc<float> {
   __device__ __forceinline__ double get() const { return (double)s - (double)c; }
 };
 
+// Warp total of per-lane accumulators, valid in lane 0.  FP64: plain
+// butterfly.  FP32: the lanes' Kahan states (value s - c) are merged in FP32
+// by error-free TwoSum steps (s1 + s2 = S + e exactly; the merged state is
+// S, c1 + c2 - e), and only lane 0 converts to FP64: on GB300 an FP64
+// instruction costs a warp about 16 SM cycles, an FP32 one a fraction of one.
+__device__ __forceinline__ double warp_total(const Acc<double>& a) { return warp_sum(a.s); }
+__device__ __forceinline__ double warp_total(const Acc<float>& a) {
+  float s = a.s, c = a.c;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const float s2 = __shfl_xor_sync(0xffffffffu, s, o);
+    const float c2 = __shfl_xor_sync(0xffffffffu, c, o);
+    const float S = __fadd_rn(s, s2);
+    const float bb = __fsub_rn(S, s);
+    const float e = __fadd_rn(__fsub_rn(s, __fsub_rn(S, bb)), __fsub_rn(s2, bb));
+    c = __fsub_rn(__fadd_rn(c, c2), e);
+    s = S;
+  }
+  return (threadIdx.x & 31) == 0 ? (double)s - (double)c : 0.0;
+}
+
+// Block total of per-thread accumulators (warp_total per warp, then the warps
+// in order in FP64); result valid in thread 0.
+template <typename V>
+__device__ __forceinline__ double block_total(const Acc<V>& a, double* sm) {
+  const double v = warp_total(a);
+  const int w = threadIdx.x >> 5;
+  if ((threadIdx.x & 31) == 0) sm[w] = v;
+  __syncthreads();
+  double s = 0.0;
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int i = 0; i < RSB_WARPS; ++i) s += sm[i];
+  }
+  __syncthreads();
+  return s;
+}
+
+// Gram-Schmidt coefficients in the vector type, converted once per CTA:
+// cv[0] = V(coef[0] / sqrt(n)) for u0, cv[k] = V(coef[k]) otherwise.
+template <typename V, bool CO>
+__device__ __forceinline__ void stage_coef(const double* coef, int nc, double isn, V* cv) {
+  for (int k = threadIdx.x; k < nc; k += RSB_BLOCK) {
+    const double c = CO ? __ldcg(coef + k) : coef[k];
+    cv[k] = k == 0 ? V(c * isn) : V(c);
+  }
+  __syncthreads();
+}
+
 // Last-CTA election of a unit's segmented reduction: every CTA of the unit
 // has stored its partials; the CTA that arrives last reduces them in tile
 // order (so the result does not depend on which CTA is last) and resets the

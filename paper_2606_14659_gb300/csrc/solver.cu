@@ -167,19 +167,20 @@ __device__ __forceinline__ void store_dots(const LzArgs<V>& a, int nc, Acc<V> (&
   for (int i = 0; i < MAXCW; ++i) {
     const int c = w + RSB_WARPS * i;
     if (c < nc) {
-      const double s = warp_sum(acc[i].get());
+      const double s = warp_total(acc[i]);
       if (lane == 0) a.partials[(long long)c * a.stride + tix] = s;
     }
   }
 }
 
-// w[rr] -= sum_c coef[c] basis_c for the RSB_SUBR rows of this thread
-// (rows base + rr*RSB_BLOCK + tid), coefficient-outer.
+// w[rr] -= sum_c cv[c] basis_c for the RSB_SUBR rows of this thread
+// (rows base + rr*RSB_BLOCK + tid), coefficient-outer; cv holds the
+// coefficients already in the vector type (stage_coef).
 template <typename V, bool CO>
-__device__ __forceinline__ void gs_update_rows(const LzArgs<V>& a, const Unit& u,
-                                               const double* coef, int nd, int nq, int base,
-                                               int end, V (&w)[RSB_SUBR]) {
-  const V c0 = V(ldc<CO>(coef) * u.isn);
+__device__ __forceinline__ void gs_update_rows(const LzArgs<V>& a, const Unit& u, const V* cv,
+                                               int nd, int nq, int base, int end,
+                                               V (&w)[RSB_SUBR]) {
+  const V c0 = cv[0];
 #pragma unroll
   for (int rr = 0; rr < RSB_SUBR; ++rr) {
     const int r = base + rr * RSB_BLOCK + threadIdx.x;
@@ -187,14 +188,14 @@ __device__ __forceinline__ void gs_update_rows(const LzArgs<V>& a, const Unit& u
   }
   for (int l = 0; l < nd; ++l) {
     const double* d = l == 0 ? a.D0 : a.D1;
-    const V cl = V(ldc<CO>(coef + 1 + l));
+    const V cl = cv[1 + l];
 #pragma unroll
     for (int rr = 0; rr < RSB_SUBR; ++rr) {
       const int r = base + rr * RSB_BLOCK + threadIdx.x;
       if (r < end) w[rr] -= cl * V(d[r]);
     }
   }
-  const double* cq = coef + 1 + nd;
+  const V* cq = cv + 1 + nd;
   bool ok[RSB_SUBR];
 #pragma unroll
   for (int rr = 0; rr < RSB_SUBR; ++rr) ok[rr] = base + rr * RSB_BLOCK + (int)threadIdx.x < end;
@@ -209,13 +210,13 @@ __device__ __forceinline__ void gs_update_rows(const LzArgs<V>& a, const Unit& u
     }
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
-      const V ck = V(ldc<CO>(cq + k + i));
+      const V ck = cq[k + i];
 #pragma unroll
       for (int rr = 0; rr < RSB_SUBR; ++rr) w[rr] -= ck * qv[i][rr];
     }
   }
   for (; k < nq; ++k) {
-    const V ck = V(ldc<CO>(cq + k));
+    const V ck = cq[k];
     const V* q = a.Q + (long long)k * a.N + base + threadIdx.x;
 #pragma unroll
     for (int rr = 0; rr < RSB_SUBR; ++rr)
@@ -244,8 +245,11 @@ __device__ __forceinline__ void lz_a_t(const LzArgs<V>& a, int j, int tix, V* ws
   const V* src = (j & 1) ? a.W1 : a.W0;
   V* dst = (j & 1) ? a.W0 : a.W1;
   V* qj = a.Q + (long long)j * a.N;
-  const double sc = 1.0 / (j == ldc<CO>(&u.j0) ? ldc<CO>(&u.beta0) : ldc<CO>(&u.beta[j]));
-  const V s = V(sc);
+  // 1 / beta once per CTA (an FP64 division per thread costs the SM's FP64 pipe)
+  if (threadIdx.x == 0)
+    out[0] = 1.0 / (j == ldc<CO>(&u.j0) ? ldc<CO>(&u.beta0) : ldc<CO>(&u.beta[j]));
+  __syncthreads();
+  const V s = V(out[0]);
   const int nd = u.nd;
   const int nc = 2 + nd + j;
   Acc<V> acc[MAXCW];
@@ -283,13 +287,15 @@ __device__ __forceinline__ void lz_a_t(const LzArgs<V>& a, int j, int tix, V* ws
 }
 
 template <typename V, bool CO>
-__device__ __forceinline__ void lz_b_t(const LzArgs<V>& a, int j, int tix, V* ws, double* out) {
+__device__ __forceinline__ void lz_b_t(const LzArgs<V>& a, int j, int tix, V* ws, V* cv,
+                                       double* out) {
   const Tile t = a.tiles[tix];
   Unit& u = a.units[t.unit];
   if (ldc<CO>(&u.status) != U_ACTIVE || j >= ldc<CO>(&u.msteps) || j < ldc<CO>(&u.j0)) return;
   V* w_ = (j & 1) ? a.W0 : a.W1;
   const int nd = u.nd;
   const int nc = 2 + nd + j;
+  stage_coef<V, CO>(u.c1, nc, u.isn, cv);
   Acc<V> acc[MAXCW];
   unsigned long long pbytes = 0;
   for (int base = t.row0; base < t.row1; base += SUBROWS) {
@@ -300,7 +306,7 @@ __device__ __forceinline__ void lz_b_t(const LzArgs<V>& a, int j, int tix, V* ws
       const int r = base + rr * RSB_BLOCK + threadIdx.x;
       w[rr] = r < end ? w_[r] : V(0);
     }
-    gs_update_rows<V, CO>(a, u, u.c1, nd, j + 1, base, end, w);
+    gs_update_rows<V, CO>(a, u, cv, nd, j + 1, base, end, w);
 #pragma unroll
     for (int rr = 0; rr < RSB_SUBR; ++rr) {
       const int r = base + rr * RSB_BLOCK + threadIdx.x;
@@ -334,12 +340,13 @@ __device__ __forceinline__ void lz_b_t(const LzArgs<V>& a, int j, int tix, V* ws
 
 template <typename V, bool CO>
 __device__ __forceinline__ void lz_c_t(const LzArgs<V>& a, int j, double breakdown, int tix,
-                                       double* sm, double* out) {
+                                       V* cv, double* sm, double* out) {
   const Tile t = a.tiles[tix];
   Unit& u = a.units[t.unit];
   if (ldc<CO>(&u.status) != U_ACTIVE || j >= ldc<CO>(&u.msteps) || j < ldc<CO>(&u.j0)) return;
   V* w_ = (j & 1) ? a.W0 : a.W1;
   const int nd = u.nd;
+  stage_coef<V, CO>(u.c2, 2 + nd + j, u.isn, cv);
   Acc<V> acc;
   unsigned long long pbytes = 0;
   for (int base = t.row0; base < t.row1; base += SUBROWS) {
@@ -350,7 +357,7 @@ __device__ __forceinline__ void lz_c_t(const LzArgs<V>& a, int j, double breakdo
       const int r = base + rr * RSB_BLOCK + threadIdx.x;
       w[rr] = r < end ? w_[r] : V(0);
     }
-    gs_update_rows<V, CO>(a, u, u.c2, nd, j + 1, base, end, w);
+    gs_update_rows<V, CO>(a, u, cv, nd, j + 1, base, end, w);
 #pragma unroll
     for (int rr = 0; rr < RSB_SUBR; ++rr) {
       const int r = base + rr * RSB_BLOCK + threadIdx.x;
@@ -362,7 +369,7 @@ __device__ __forceinline__ void lz_c_t(const LzArgs<V>& a, int j, double breakdo
     }
   }
   if (a.pb_c) prof_add(a.pb_c, pbytes);
-  const double sum = block_sum(acc.get(), sm);
+  const double sum = block_total(acc, sm);
   if (threadIdx.x == 0) a.partials[tix] = sum;
   if (last_cta(&u.cnt, u.ntile)) {
     final_reduce(a.partials, a.stride, u.tile0, u.ntile, 1, out);
@@ -387,15 +394,17 @@ __global__ void __launch_bounds__(RSB_BLOCK, 2) k_lz_a(LzArgs<V> a, int j) {
 template <typename V>
 __global__ void __launch_bounds__(RSB_BLOCK, 2) k_lz_b(LzArgs<V> a, int j) {
   __shared__ V ws[SUBROWS];
+  __shared__ V cv[RSB_MAXC];
   __shared__ double out[RSB_MAXC];
-  lz_b_t<V, false>(a, j, blockIdx.x, ws, out);
+  lz_b_t<V, false>(a, j, blockIdx.x, ws, cv, out);
 }
 
 template <typename V>
 __global__ void __launch_bounds__(RSB_BLOCK) k_lz_c(LzArgs<V> a, int j, double breakdown) {
   __shared__ double sm[RSB_WARPS];
+  __shared__ V cv[RSB_MAXC];
   __shared__ double out[1];
-  lz_c_t<V, false>(a, j, breakdown, blockIdx.x, sm, out);
+  lz_c_t<V, false>(a, j, breakdown, blockIdx.x, cv, sm, out);
 }
 
 // ----------------------------------------------------------------------------
@@ -786,14 +795,15 @@ __global__ void __launch_bounds__(RSB_BLOCK, 2)
   __shared__ CycleShared<V> sh;
   __shared__ double out[RSB_MAXC];
   __shared__ double sm[RSB_WARPS];
+  __shared__ V cv[RSB_MAXC];
   V* ws = reinterpret_cast<V*>(sh.wsd);
   const unsigned G = gridDim.x;
   for (int j = jstart; j < M; ++j) {
     for (int t = blockIdx.x; t < ntiles; t += G) lz_a_t<V, true>(a, j, t, ws, out);
     if (!grid_sync(gb, G)) return;
-    for (int t = blockIdx.x; t < ntiles; t += G) lz_b_t<V, true>(a, j, t, ws, out);
+    for (int t = blockIdx.x; t < ntiles; t += G) lz_b_t<V, true>(a, j, t, ws, cv, out);
     if (!grid_sync(gb, G)) return;
-    for (int t = blockIdx.x; t < ntiles; t += G) lz_c_t<V, true>(a, j, breakdown, t, sm, out);
+    for (int t = blockIdx.x; t < ntiles; t += G) lz_c_t<V, true>(a, j, breakdown, t, cv, sm, out);
     if (!grid_sync(gb, G)) return;
   }
   for (int u = blockIdx.x; u < nunits; u += G) lz_eig_u<V, true>(a.units[u], unit_S(a.S, u), sh.J);
@@ -817,21 +827,23 @@ __global__ void __launch_bounds__(RSB_BLOCK, 2)
 // operand, the reduction partials and the per-unit scalars.  Steps, their
 // order, the per-thread accumulation order and the reductions are those of
 // the streaming kernels above, so both modes give the same numbers.
-// Shared layout: JacShared | coefficients | w of the tile | Q[k * trs + rl].
+// Shared layout: JacShared | coefficients (FP64, and in the vector type) | w of
+// the tile | deflation vectors of the tile | Q[k * trs + rl].
 // ----------------------------------------------------------------------------
 __host__ __device__ constexpr size_t res_align(size_t b) { return (b + 15) & ~(size_t)15; }
 
 template <typename V>
 __host__ __device__ constexpr size_t res_smem_bytes(int M, int trs) {
   return res_align(sizeof(JacShared<V>)) + res_align(2 * sizeof(double) * RSB_MAXC) +
-         res_align(sizeof(V) * (size_t)trs) + sizeof(V) * (size_t)M * (size_t)trs;
+         res_align(2 * sizeof(V) * RSB_MAXC) + res_align(sizeof(V) * (size_t)trs) +
+         res_align(sizeof(V) * RSB_MAXD * (size_t)trs) + sizeof(V) * (size_t)M * (size_t)trs;
 }
 
 // Dots of [1, D, q_0..] with the tile's w: the coefficient split across warps
 // and the per-lane row order of tile_dots.
 template <typename V>
-__device__ __forceinline__ void res_dots(const LzArgs<V>& a, const Tile& t, int nd, int nc,
-                                         const V* Qs, int trs, const V* ws,
+__device__ __forceinline__ void res_dots(const Tile& t, int nd, int nc, const V* Qs,
+                                         const V* Ds, int trs, const V* ws,
                                          Acc<V> (&acc)[MAXCW]) {
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nr = t.row1 - t.row0;
@@ -842,8 +854,8 @@ __device__ __forceinline__ void res_dots(const LzArgs<V>& a, const Tile& t, int 
       if (c == 0) {
         for (int rl = lane; rl < nr; rl += 32) acc[i].add(V(1) * ws[rl]);
       } else if (c <= nd) {
-        const double* d = c == 1 ? a.D0 : a.D1;
-        for (int rl = lane; rl < nr; rl += 32) acc[i].add(V(d[t.row0 + rl]) * ws[rl]);
+        const V* d = Ds + (size_t)(c - 1) * trs;
+        for (int rl = lane; rl < nr; rl += 32) acc[i].add(d[rl] * ws[rl]);
       } else {
         const V* q = Qs + (size_t)(c - 1 - nd) * trs;
         for (int rl = lane; rl < nr; rl += 32) acc[i].add(q[rl] * ws[rl]);
@@ -852,15 +864,15 @@ __device__ __forceinline__ void res_dots(const LzArgs<V>& a, const Tile& t, int 
   }
 }
 
-// w -= [1/sqrt(n), D, q_0..q_{nq-1}] cf, in the order of gs_update_rows.
+// w -= [1/sqrt(n), D, q_0..q_{nq-1}] cv, in the order of gs_update_rows (cv:
+// the coefficients in the vector type; in_unit: the row belongs to the unit).
 template <typename V>
-__device__ __forceinline__ V res_upd_row(const LzArgs<V>& a, const Unit& u, const double* cf,
-                                         int nd, int nq, const V* Qs, int trs, int rl, int r,
-                                         V w) {
-  if (unit_has(u, a.ckey, r)) w -= V(cf[0] * u.isn);
-  for (int l = 0; l < nd; ++l) w -= V(cf[1 + l]) * V((l == 0 ? a.D0 : a.D1)[r]);
-  const double* cq = cf + 1 + nd;
-  for (int k = 0; k < nq; ++k) w -= V(cq[k]) * Qs[(size_t)k * trs + rl];
+__device__ __forceinline__ V res_upd_row(const V* cv, int nd, int nq, const V* Qs,
+                                         const V* Ds, int trs, int rl, bool in_unit, V w) {
+  if (in_unit) w -= cv[0];
+  for (int l = 0; l < nd; ++l) w -= cv[1 + l] * Ds[(size_t)l * trs + rl];
+  const V* cq = cv + 1 + nd;
+  for (int k = 0; k < nq; ++k) w -= cq[k] * Qs[(size_t)k * trs + rl];
   return w;
 }
 
@@ -872,7 +884,7 @@ __device__ __forceinline__ void res_store_dots(double* P, long long stride, int 
   for (int i = 0; i < MAXCW; ++i) {
     const int c = w + RSB_WARPS * i;
     if (c < nc) {
-      const double s = warp_sum(acc[i].get());
+      const double s = warp_total(acc[i]);
       if (lane == 0) P[(long long)c * stride + tix] = s;
     }
   }
@@ -885,13 +897,12 @@ __device__ __forceinline__ void res_store_dots(double* P, long long stride, int 
 // between two partial buffers: a buffer is rewritten only after a barrier
 // that follows every CTA's reduction of its previous contents.
 //
-// A(j): q_j = src * sc into shared memory, w = L q_j, dots [1, D, q_0..q_j]^T w.
+// A(j): q_j = src * s into shared memory, w = L q_j, dots [1, D, q_0..q_j]^T w.
 template <typename V>
-__device__ void res_a(const LzArgs<V>& a, int j, double sc, int tix, const Tile& t,
-                      const Unit& u, V* Qs, int trs, V* ws, double* P) {
+__device__ void res_a(const LzArgs<V>& a, int j, V s, int tix, const Tile& t, const Unit& u,
+                      V* Qs, const V* Ds, int trs, V* ws, double* P) {
   const int nr = t.row1 - t.row0;
   const V* src = (j & 1) ? a.W1 : a.W0;
-  const V s = V(sc);
   const int nd = u.nd;
   const int nc = 2 + nd + j;
   unsigned long long pbytes = 0;
@@ -906,56 +917,63 @@ __device__ void res_a(const LzArgs<V>& a, int j, double sc, int tix, const Tile&
   }
   __syncthreads();
   Acc<V> acc[MAXCW];
-  res_dots<V>(a, t, nd, nc, Qs, trs, ws, acc);
+  res_dots<V>(t, nd, nc, Qs, Ds, trs, ws, acc);
   res_store_dots<V>(P, a.stride, nc, acc, tix);
   if (a.pb_a) prof_add(a.pb_a, pbytes);
 }
 
 // B(j): w -= basis c1, dots of the result (second pass).
 template <typename V>
-__device__ void res_b(const LzArgs<V>& a, int j, int tix, const Tile& t, const Unit& u,
-                      const V* Qs, int trs, V* ws, const double* c1, double* P) {
+__device__ void res_b(const LzArgs<V>& a, int j, int tix, const Tile& t, int nd, bool masked,
+                      uint64_t key, const V* Qs, const V* Ds, int trs, V* ws, const V* cv,
+                      double* P) {
   const int nr = t.row1 - t.row0;
-  const int nd = u.nd;
   const int nc = 2 + nd + j;
   unsigned long long pbytes = 0;
   for (int rl = threadIdx.x; rl < nr; rl += RSB_BLOCK) {
-    const int r = t.row0 + rl;
-    ws[rl] = res_upd_row<V>(a, u, c1, nd, j + 1, Qs, trs, rl, r, ws[rl]);
+    const bool in_unit = !masked || a.ckey[t.row0 + rl] == key;
+    ws[rl] = res_upd_row<V>(cv, nd, j + 1, Qs, Ds, trs, rl, in_unit, ws[rl]);
     if (a.pb_b) pbytes += sizeof(V) * (unsigned long long)(3 + j) + 8ull * nd;
   }
   __syncthreads();
   Acc<V> acc[MAXCW];
-  res_dots<V>(a, t, nd, nc, Qs, trs, ws, acc);
+  res_dots<V>(t, nd, nc, Qs, Ds, trs, ws, acc);
   res_store_dots<V>(P, a.stride, nc, acc, tix);
   if (a.pb_b) prof_add(a.pb_b, pbytes);
 }
 
 // C(j): w -= basis c2 into W[(j + 1) & 1] (the next SpMV operand), ||w||^2.
 template <typename V>
-__device__ void res_c(const LzArgs<V>& a, int j, int tix, const Tile& t, const Unit& u,
-                      const V* Qs, int trs, const V* ws, const double* c2, double* sm,
-                      double* P) {
+__device__ void res_c(const LzArgs<V>& a, int j, int tix, const Tile& t, int nd, bool masked,
+                      uint64_t key, const V* Qs, const V* Ds, int trs, const V* ws,
+                      const V* cv, double* sm, double* P) {
   const int nr = t.row1 - t.row0;
-  const int nd = u.nd;
   V* dst = (j & 1) ? a.W0 : a.W1;
   Acc<V> acc;
   unsigned long long pbytes = 0;
   for (int rl = threadIdx.x; rl < nr; rl += RSB_BLOCK) {
-    const int r = t.row0 + rl;
-    const V w = res_upd_row<V>(a, u, c2, nd, j + 1, Qs, trs, rl, r, ws[rl]);
-    dst[r] = w;
+    const bool in_unit = !masked || a.ckey[t.row0 + rl] == key;
+    const V w = res_upd_row<V>(cv, nd, j + 1, Qs, Ds, trs, rl, in_unit, ws[rl]);
+    dst[t.row0 + rl] = w;
     acc.add(w * w);
     if (a.pb_c) pbytes += sizeof(V) * (unsigned long long)(3 + j) + 8ull * nd;
   }
   if (a.pb_c) prof_add(a.pb_c, pbytes);
-  const double sum = block_sum(acc.get(), sm);
+  const double sum = block_total(acc, sm);
   if (threadIdx.x == 0) P[tix] = sum;
 }
 
-// coefficients of a finished reduction: c[0] carries the 1/sqrt(n) of u0
-__device__ __forceinline__ void res_coef(const double* out, int nc, double isn, double* c) {
-  for (int k = threadIdx.x; k < nc; k += RSB_BLOCK) c[k] = k == 0 ? out[0] * isn : out[k];
+// coefficients of a finished reduction: c[0] carries the 1/sqrt(n) of u0 (as
+// the streaming kernels store it); cv the same in the vector type, cv[0]
+// already times 1/sqrt(n) again (the u0 component of the update)
+template <typename V>
+__device__ __forceinline__ void res_coef(const double* out, int nc, double isn, double* c,
+                                         V* cv) {
+  for (int k = threadIdx.x; k < nc; k += RSB_BLOCK) {
+    const double v = k == 0 ? out[0] * isn : out[k];
+    c[k] = v;
+    cv[k] = k == 0 ? V(v * isn) : V(v);
+  }
   __syncthreads();
 }
 
@@ -1005,17 +1023,35 @@ __global__ void __launch_bounds__(RSB_BLOCK, 2)
   double* c1 = reinterpret_cast<double*>(res_sh + off);
   double* c2 = c1 + RSB_MAXC;
   off += res_align(2 * sizeof(double) * RSB_MAXC);
+  V* cv1 = reinterpret_cast<V*>(res_sh + off);
+  V* cv2 = cv1 + RSB_MAXC;
+  off += res_align(2 * sizeof(V) * RSB_MAXC);
   V* ws = reinterpret_cast<V*>(res_sh + off);
   off += res_align(sizeof(V) * (size_t)trs);
+  V* Ds = reinterpret_cast<V*>(res_sh + off);
+  off += res_align(sizeof(V) * RSB_MAXD * (size_t)trs);
   V* Qs = reinterpret_cast<V*>(res_sh + off);
   __shared__ double out[RSB_MAXC];
   __shared__ double sm[RSB_WARPS];
+  __shared__ double beta_sh;
+  __shared__ V scale_sh;
   const unsigned G = gridDim.x;
   const int tix = blockIdx.x;
   const Tile t = a.tiles[tix];
   Unit& u = a.units[t.unit];
+  const int nr = t.row1 - t.row0;
+  const int nd = u.nd;
+  const bool masked = u.masked;
+  const uint64_t key = u.key;
+  const double isn = u.isn;
   const bool lead = tix == u.tile0 && threadIdx.x == 0;
   double* const Pb[2] = {a.partials, a.partials + (long long)RSB_MAXC * a.stride};
+  // the tile's deflation vectors in the vector type, once per solve
+  for (int l = 0; l < nd; ++l) {
+    const double* d = l == 0 ? a.D0 : a.D1;
+    for (int rl = threadIdx.x; rl < nr; rl += RSB_BLOCK) Ds[(size_t)l * trs + rl] = V(d[t.row0 + rl]);
+  }
+  __syncthreads();
   int* jm = a.jmin;  // two slots: read one at a cycle's start, refill the other
   for (int cyc = 0; cyc < maxcyc; ++cyc) {
     const int jstart = cyc == 0 ? 0 : min(max(__ldcg(jm + (cyc & 1)), 0), M);
@@ -1026,23 +1062,26 @@ __global__ void __launch_bounds__(RSB_BLOCK, 2)
     const bool on = __ldcg(&u.status) == U_ACTIVE;
     const int j0 = __ldcg(&u.j0);
     int msteps = __ldcg(&u.msteps);
-    double beta = __ldcg(&u.beta0);
-    const int nd = u.nd;
+    if (threadIdx.x == 0) {
+      beta_sh = __ldcg(&u.beta0);
+      scale_sh = V(1.0 / beta_sh);
+    }
+    __syncthreads();
     int ph = 0;
     for (int j = jstart; j < M; ++j) {
       const bool st = on && j < msteps && j >= j0;
       const int nc = 2 + nd + j;
-      if (st) res_a<V>(a, j, 1.0 / beta, tix, t, u, Qs, trs, ws, Pb[ph & 1]);
+      if (st) res_a<V>(a, j, scale_sh, tix, t, u, Qs, Ds, trs, ws, Pb[ph & 1]);
       if (!grid_sync(gb, G)) return;
       if (st) {
         final_reduce(Pb[ph & 1], a.stride, u.tile0, u.ntile, nc, out);
-        res_coef(out, nc, u.isn, c1);
-        res_b<V>(a, j, tix, t, u, Qs, trs, ws, c1, Pb[(ph + 1) & 1]);
+        res_coef<V>(out, nc, isn, c1, cv1);
+        res_b<V>(a, j, tix, t, nd, masked, key, Qs, Ds, trs, ws, cv1, Pb[(ph + 1) & 1]);
       }
       if (!grid_sync(gb, G)) return;
       if (st) {
         final_reduce(Pb[(ph + 1) & 1], a.stride, u.tile0, u.ntile, nc, out);
-        res_coef(out, nc, u.isn, c2);
+        res_coef<V>(out, nc, isn, c2, cv2);
         if (tix == u.tile0) {  // column j of S = Q^T L Q
           double* Sm = unit_S(a.S, t.unit);
           for (int k = threadIdx.x; k <= j; k += RSB_BLOCK) {
@@ -1051,20 +1090,23 @@ __global__ void __launch_bounds__(RSB_BLOCK, 2)
             Sm[j * RSB_MAXM + k] = v;
           }
         }
-        res_c<V>(a, j, tix, t, u, Qs, trs, ws, c2, sm, Pb[ph & 1]);
+        res_c<V>(a, j, tix, t, nd, masked, key, Qs, Ds, trs, ws, cv2, sm, Pb[ph & 1]);
       }
       if (!grid_sync(gb, G)) return;
       if (st) {
         final_reduce(Pb[ph & 1], a.stride, u.tile0, u.ntile, 1, out);
-        beta = sqrt(out[0]);
-        if (lead) u.beta[j + 1] = beta;
-        if (beta <= breakdown * u.dmax) {  // invariant subspace: the cycle ends here
-          msteps = j + 1;
-          if (lead) {
+        if (threadIdx.x == 0) {
+          const double b = sqrt(out[0]);
+          beta_sh = b;
+          scale_sh = V(1.0 / b);
+          if (lead) u.beta[j + 1] = b;
+          if (b <= breakdown * u.dmax && lead) {  // invariant subspace: the cycle ends here
             u.msteps = j + 1;
             u.broke = 1;
           }
         }
+        __syncthreads();
+        if (beta_sh <= breakdown * u.dmax) msteps = j + 1;
       }
       ++ph;
     }
