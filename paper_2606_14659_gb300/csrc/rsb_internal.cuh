@@ -328,38 +328,37 @@ __device__ __forceinline__ T ldc(const T* p) {
 }
 
 // out[c] = sum_t partials[c * stride + t0 + t], t in [0, nt), c in [0, nc);
-// fixed order (lane-strided then butterfly), executed by the whole CTA.
+// fixed order, executed by the whole CTA.  Warp w owns coefficients w, w + 8,
+// ...; eight lanes share a coefficient (four coefficients per warp at a
+// time): lane s of a group adds tiles s, s + 8, ... (loads issued four at a
+// time), then a three-level butterfly.  The FP64 adds are the cost on GB300
+// (one FP64 warp instruction per ~64 cycles of an SM sub-partition), so no
+// coefficient takes a 32-lane butterfly and unused coefficient slots cost
+// nothing.
 __device__ __forceinline__ void final_reduce(const double* partials, long long stride, int t0,
                                              int nt, int nc, double* out) {
-  // warp w owns coefficients w, w + 8, ...; every lane issues the loads of all
-  // of its warp's coefficients for 4 tiles before adding, so one batch costs one
-  // round trip to L2 instead of one per coefficient
   constexpr int CW = (RSB_MAXC + RSB_WARPS - 1) / RSB_WARPS;
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  double acc[CW];
-#pragma unroll
-  for (int i = 0; i < CW; ++i) acc[i] = 0.0;
-  for (int tb = 0; tb < nt; tb += 128) {
-    double v[CW][4];
-#pragma unroll
-    for (int i = 0; i < CW; ++i) {
-      const int c = w + RSB_WARPS * i;
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const int t = tb + lane + 32 * q;
-        v[i][q] = (c < nc && t < nt) ? __ldcg(partials + (long long)c * stride + t0 + t) : 0.0;
+  const int g = lane >> 3, s = lane & 7;
+  for (int pass = 0; pass < CW; pass += 4) {
+    if (w + RSB_WARPS * pass >= nc) break;  // no coefficient of this warp is left
+    const int c = w + RSB_WARPS * (pass + g);
+    const bool on = pass + g < CW && c < nc;
+    double acc = 0.0;
+    if (on) {
+      const double* p = partials + (long long)c * stride + t0;
+      int t = s;
+      for (; t + 24 < nt; t += 32) {
+        const double a0 = __ldcg(p + t), a1 = __ldcg(p + t + 8);
+        const double a2 = __ldcg(p + t + 16), a3 = __ldcg(p + t + 24);
+        acc += (a0 + a1) + (a2 + a3);
       }
+      for (; t < nt; t += 8) acc += __ldcg(p + t);
     }
-#pragma unroll
-    for (int i = 0; i < CW; ++i) acc[i] += (v[i][0] + v[i][1]) + (v[i][2] + v[i][3]);
-  }
-#pragma unroll
-  for (int i = 0; i < CW; ++i) {
-    const int c = w + RSB_WARPS * i;
-    if (c < nc) {
-      const double s = warp_sum(acc[i]);
-      if (lane == 0) out[c] = s;
-    }
+    acc += __shfl_xor_sync(0xffffffffu, acc, 4);
+    acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+    acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+    if (on && s == 0) out[c] = acc;
   }
   __syncthreads();
 }
