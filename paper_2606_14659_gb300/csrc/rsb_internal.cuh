@@ -286,23 +286,35 @@ __device__ __forceinline__ unsigned long long global_ns() {
   return t;
 }
 
+// Arrival is an acquire-release add on the counter (it publishes the CTA's
+// writes, which the CTA barrier ordered before it, and observes those of the
+// CTAs that arrived earlier); the last CTA resets the counter and releases the
+// next generation; the others spin on an acquire load of the generation.
+__device__ __forceinline__ unsigned atom_add_acq_rel(unsigned* p, unsigned v) {
+  unsigned old;
+  asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+  return old;
+}
+__device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
 __device__ __forceinline__ bool grid_sync(GridBar* b, unsigned nblocks) {
   __shared__ int s_ok;
   __syncthreads();
   if (threadIdx.x == 0) {
-    volatile unsigned int* vgen = &b->gen;
     volatile int* verr = &b->err;
-    const unsigned g = *vgen;
-    __threadfence();
-    const unsigned arrived = atomicAdd(&b->count, 1u);
+    const unsigned g = ld_acquire(&b->gen);
+    const unsigned arrived = atom_add_acq_rel(&b->count, 1u);
     if (arrived == nblocks - 1) {
-      b->count = 0u;
-      __threadfence();
-      atomicAdd(&b->gen, 1u);
+      asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(&b->count), "r"(0u) : "memory");
+      asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(&b->gen), "r"(1u) : "memory");
     } else {
       const unsigned long long t0 = global_ns();
       unsigned spins = 0;
-      while (*vgen == g) {
+      while (ld_acquire(&b->gen) == g) {
         if (*verr) break;
         ++spins;
         if ((spins & 255u) == 0 && global_ns() - t0 > 4000000000ull) {
@@ -312,7 +324,6 @@ __device__ __forceinline__ bool grid_sync(GridBar* b, unsigned nblocks) {
         if (spins > 32) __nanosleep(32);
       }
     }
-    __threadfence();
     s_ok = (*verr == 0);
   }
   __syncthreads();
