@@ -39,7 +39,7 @@
 #define RSB_SSTRIDE (2 * RSB_MAXM * RSB_MAXM)  // doubles of S and Y per unit
 #define RSB_MAXTILES_PER_UNIT 1024
 #define RSB_MINR 2    // minimum rows per thread of a tile
-#define RSB_SUBR 8    // rows per thread handled between two CTA barriers
+#define RSB_SUBR 4    // rows per thread handled between two CTA barriers
 #define RSB_COLBITS 29
 #define RSB_COLMASK 0x1FFFFFFFu
 #define RSB_MAXN (1 << RSB_COLBITS)

@@ -385,14 +385,14 @@ __device__ __forceinline__ void lz_c_t(const LzArgs<V>& a, int j, double breakdo
 }
 
 template <typename V>
-__global__ void __launch_bounds__(RSB_BLOCK, 2) k_lz_a(LzArgs<V> a, int j) {
+__global__ void __launch_bounds__(RSB_BLOCK, sizeof(V) == 4 ? 3 : 2) k_lz_a(LzArgs<V> a, int j) {
   __shared__ V ws[SUBROWS];
   __shared__ double out[RSB_MAXC];
   lz_a_t<V, false>(a, j, blockIdx.x, ws, out);
 }
 
 template <typename V>
-__global__ void __launch_bounds__(RSB_BLOCK, 2) k_lz_b(LzArgs<V> a, int j) {
+__global__ void __launch_bounds__(RSB_BLOCK, sizeof(V) == 4 ? 3 : 2) k_lz_b(LzArgs<V> a, int j) {
   __shared__ V ws[SUBROWS];
   __shared__ V cv[RSB_MAXC];
   __shared__ double out[RSB_MAXC];
