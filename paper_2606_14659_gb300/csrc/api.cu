@@ -470,8 +470,12 @@ static int reserve_prec(Ctx& c, int f32, int64_t N, int M, SolveBufs& B) {
   PrecBufs& p = c.pb[f32 ? 1 : 0];
   const size_t es = f32 ? sizeof(float) : sizeof(double);
   const size_t vb = es * (size_t)(N + 32);
+  // basis stride: a multiple of 32 rows with 4 rows to spare, so every vector
+  // starts 128-byte aligned and a chunk copy rounded out to 16 bytes stays
+  // inside its vector (bulk copies need 16-byte addresses and sizes)
+  const int64_t ldN = (N + 4 + 31) / 32 * 32;
   int rc;
-  if ((rc = devbuf_reserve(p.Q, vb * (size_t)M))) return rc;
+  if ((rc = devbuf_reserve(p.Q, es * (size_t)ldN * (size_t)M + 256))) return rc;
   if ((rc = devbuf_reserve(p.W0, vb))) return rc;
   if ((rc = devbuf_reserve(p.W1, vb))) return rc;
   if ((rc = devbuf_reserve(p.Y, vb))) return rc;
@@ -487,7 +491,7 @@ static int reserve_prec(Ctx& c, int f32, int64_t N, int M, SolveBufs& B) {
   B.R = p.R.p;
   B.P = p.P.p;
   B.AP = p.AP.p;
-  B.N = N;
+  B.N = ldN;
   Counters* cn = dptr<Counters>(c.counters);
   B.n_active = &cn->n_active;
   B.n_cg = &cn->n_cg;

@@ -408,6 +408,172 @@ __global__ void __launch_bounds__(RSB_BLOCK) k_lz_c(LzArgs<V> a, int j, double b
 }
 
 // ----------------------------------------------------------------------------
+// Step B with the basis staged by TMA (launch modes 0 and 1).  The tile is
+// walked in chunks of RSB_BLOCK rows; for every chunk one thread issues 1-D
+// bulk copies (cp.async.bulk, completion counted in bytes on an mbarrier) of
+// the chunk's rows of q_0..q_j into shared memory, one chunk ahead of the one
+// being computed (two buffers).  The update and the second-pass dots then
+// read the basis from shared memory, so DRAM sees each basis vector once per
+// launch.  The per-row update order and the per-lane dot order are those of
+// lz_b_t and the resident kernel.  Waits on the mbarrier are bounded (2 s of
+// the global timer): on timeout the CTA sets the grid error word, waits
+// (bounded) for its own copies still in flight and returns.
+// ----------------------------------------------------------------------------
+__device__ __forceinline__ unsigned smem_addr(const void* p) {
+  return (unsigned)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity,
+                                                  unsigned long long limit_ns) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const unsigned long long t0 = global_ns();
+  while (!mbar_try_wait(bar, parity))
+    if (global_ns() - t0 > limit_ns) return false;
+  return true;
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes,
+                                         uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+          "r"(smem_addr(dst)),
+      "l"(src), "r"(bytes), "r"(smem_addr(bar))
+      : "memory");
+}
+
+template <typename V>
+struct BulkRows {
+  static constexpr int AL = 16 / sizeof(V);        // rows per 16 bytes
+  static constexpr int CRB = RSB_BLOCK + AL;       // staged rows per vector and buffer
+};
+
+template <typename V>
+constexpr size_t lz_bt_smem(int nq) {
+  return 2 * (size_t)nq * BulkRows<V>::CRB * sizeof(V);
+}
+
+template <typename V>
+__global__ void __launch_bounds__(RSB_BLOCK, 2) k_lz_bt(LzArgs<V> a, int j, GridBar* gb) {
+  extern __shared__ __align__(128) unsigned char bt_sh[];
+  constexpr int AL = BulkRows<V>::AL, CRB = BulkRows<V>::CRB;
+  __shared__ __align__(8) uint64_t bar[2];
+  __shared__ V ws[RSB_BLOCK];
+  __shared__ V cv[RSB_MAXC];
+  __shared__ double out[RSB_MAXC];
+  const Tile t = a.tiles[blockIdx.x];
+  Unit& u = a.units[t.unit];
+  if (u.status != U_ACTIVE || j >= u.msteps || j < u.j0) return;
+  V* Qb = reinterpret_cast<V*>(bt_sh);  // [2][nq][CRB]
+  const int nd = u.nd;
+  const int nc = 2 + nd + j;
+  const int nq = j + 1;
+  V* w_ = (j & 1) ? a.W0 : a.W1;
+  const int nchunk = (t.row1 - t.row0 + RSB_BLOCK - 1) / RSB_BLOCK;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  stage_coef<V, false>(u.c1, nc, u.isn, cv);  // ends with a CTA barrier
+  auto issue = [&](int ci) {  // thread 0: rows of chunk ci of q_0..q_j into buffer ci & 1
+    const int c0 = t.row0 + ci * RSB_BLOCK;
+    const int c1 = min(t.row1, c0 + RSB_BLOCK);
+    const int a0 = c0 & ~(AL - 1);
+    const int len = (c1 - a0 + AL - 1) / AL * AL;
+    const unsigned bytes = (unsigned)(len * sizeof(V));
+    uint64_t* b = &bar[ci & 1];
+    V* dst = Qb + (size_t)(ci & 1) * nq * CRB;
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    mbar_expect_tx(b, bytes * (unsigned)nq);
+    for (int k = 0; k < nq; ++k)
+      bulk_g2s(dst + (size_t)k * CRB, a.Q + (long long)k * a.N + a0, bytes, b);
+  };
+  if (threadIdx.x == 0) issue(0);
+  Acc<V> acc[MAXCW];
+  unsigned long long pbytes = 0;
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int ci = 0; ci < nchunk; ++ci) {
+    if (threadIdx.x == 0 && ci + 1 < nchunk) issue(ci + 1);
+    const bool ok = mbar_wait_bounded(&bar[ci & 1], (ci >> 1) & 1, 2000000000ull);
+    if (__syncthreads_or(!ok)) {
+      // copies that never completed: flag, drain what is still in flight, stop
+      if (threadIdx.x == 0) {
+        atomicExch(&gb->err, 1);
+        mbar_wait_bounded(&bar[ci & 1], (ci >> 1) & 1, 1000000000ull);
+        if (ci + 1 < nchunk) mbar_wait_bounded(&bar[(ci + 1) & 1], ((ci + 1) >> 1) & 1, 1000000000ull);
+      }
+      __syncthreads();
+      return;
+    }
+    const int c0 = t.row0 + ci * RSB_BLOCK;
+    const int c1 = min(t.row1, c0 + RSB_BLOCK);
+    const V* Qc = Qb + (size_t)(ci & 1) * nq * CRB + (c0 - (c0 & ~(AL - 1)));
+    const int r = c0 + threadIdx.x;
+    V wv = V(0);
+    if (r < c1) {
+      wv = w_[r];
+      if (unit_has(u, a.ckey, r)) wv -= cv[0];
+      for (int l = 0; l < nd; ++l) wv -= cv[1 + l] * V((l == 0 ? a.D0 : a.D1)[r]);
+      const V* cq = cv + 1 + nd;
+      for (int k = 0; k < nq; ++k) wv -= cq[k] * Qc[(size_t)k * CRB + threadIdx.x];
+      w_[r] = wv;
+      if (a.pb_b) pbytes += sizeof(V) * (unsigned long long)(3 + j) + 8ull * nd;
+    }
+    ws[threadIdx.x] = wv;
+    __syncthreads();
+    const int nr = c1 - c0;
+#pragma unroll
+    for (int i = 0; i < MAXCW; ++i) {
+      const int c = w + RSB_WARPS * i;
+      if (c < nc) {
+        if (c == 0) {
+          for (int rl = lane; rl < nr; rl += 32) acc[i].add(V(1) * ws[rl]);
+        } else if (c <= nd) {
+          const double* d = c == 1 ? a.D0 : a.D1;
+          for (int rl = lane; rl < nr; rl += 32) acc[i].add(V(d[c0 + rl]) * ws[rl]);
+        } else {
+          const V* q = Qc + (size_t)(c - 1 - nd) * CRB;
+          for (int rl = lane; rl < nr; rl += 32) acc[i].add(q[rl] * ws[rl]);
+        }
+      }
+    }
+    __syncthreads();
+  }
+  store_dots<V>(a, nc, acc, blockIdx.x);
+  if (a.pb_b) prof_add(a.pb_b, pbytes);
+  if (last_cta(&u.cnt, u.ntile)) {
+    final_reduce(a.partials, a.stride, u.tile0, u.ntile, nc, out);
+    if (threadIdx.x == 0) {
+      u.c2[0] = out[0] * u.isn;
+      for (int c = 1; c < nc; ++c) u.c2[c] = out[c];
+    }
+    __syncthreads();
+    double* Sm = unit_S(a.S, t.unit);
+    for (int k = threadIdx.x; k <= j; k += RSB_BLOCK) {
+      const double v = u.c1[1 + nd + k] + out[1 + nd + k];
+      Sm[k * RSB_MAXM + j] = v;
+      Sm[j * RSB_MAXM + k] = v;
+    }
+  }
+}
+
+// ----------------------------------------------------------------------------
 // Ritz pairs of S (K x K, K <= 40): parallel cyclic Jacobi in one CTA (FP64).
 // Rounds of the round-robin ("circle") ordering rotate K/2 disjoint pairs at
 // once; each rotation is the symmetric 2x2 Schur rotation (Golub & Van Loan
@@ -1249,15 +1415,21 @@ static int lz_start(LzArgs<V>& a, int ntiles, uint64_t sd, const double* from64,
 }
 
 template <typename V>
-static int lz_cycle(LzArgs<V>& a, int ntiles, int nunits, int M, double breakdown, cudaStream_t s) {
+static int lz_cycle(LzArgs<V>& a, int ntiles, int nunits, int M, double breakdown, GridBar* gb,
+                    cudaStream_t s) {
   for (int j = 0; j < M; ++j) {
     int pi = prof_before(PROF_LZ_A, s);
     k_lz_a<V><<<ntiles, RSB_BLOCK, 0, s>>>(a, j);
     RSB_CKL("k_lz_a");
     prof_after(pi, s);
     pi = prof_before(PROF_LZ_B, s);
-    k_lz_b<V><<<ntiles, RSB_BLOCK, 0, s>>>(a, j);
-    RSB_CKL("k_lz_b");
+    if (sizeof(V) == 4) {  // FP32: bandwidth-bound, basis staged by bulk copies
+      k_lz_bt<V><<<ntiles, RSB_BLOCK, lz_bt_smem<V>(j + 1), s>>>(a, j, gb);
+      RSB_CKL("k_lz_bt");
+    } else {  // FP64: bound by GB300's FP64 rate; the register-streaming kernel is faster
+      k_lz_b<V><<<ntiles, RSB_BLOCK, 0, s>>>(a, j);
+      RSB_CKL("k_lz_b");
+    }
     prof_after(pi, s);
     pi = prof_before(PROF_LZ_C, s);
     k_lz_c<V><<<ntiles, RSB_BLOCK, 0, s>>>(a, j, breakdown);
@@ -1345,13 +1517,18 @@ static int lanczos_run(const LevelGraph& G, const Tile* tiles, int ntiles, Unit*
     }
     return rc;
   }
+  // the staged step B (FP32) needs up to 2 * M * (RSB_BLOCK + 4) floats of
+  // dynamic shared memory (83 KB at M = 40)
+  if (sizeof(V) == 4)
+    RSB_CK(cudaFuncSetAttribute(k_lz_bt<V>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)lz_bt_smem<V>(M)));
   cudaGraphExec_t exec = nullptr;
   std::vector<int> cap_pairs;
   if (use_graph) {
     cudaGraph_t graph = nullptr;
     RSB_CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
     prof_capture_begin();
-    rc = lz_cycle<V>(a, ntiles, nunits, M, breakdown, s);
+    rc = lz_cycle<V>(a, ntiles, nunits, M, breakdown, B.gb, s);
     cap_pairs = prof_capture_end();
     cudaGraph_t g2 = nullptr;
     cudaError_t e = cudaStreamEndCapture(s, &g2);
@@ -1375,7 +1552,7 @@ static int lanczos_run(const LevelGraph& G, const Tile* tiles, int ntiles, Unit*
       }
       prof_replay(cap_pairs);
     } else {
-      rc = lz_cycle<V>(a, ntiles, nunits, M, breakdown, s);
+      rc = lz_cycle<V>(a, ntiles, nunits, M, breakdown, B.gb, s);
       if (rc) return rc;
     }
     rc = read_active(B, s, &active);
