@@ -468,6 +468,38 @@ constexpr size_t lz_bt_smem(int nq) {
   return 2 * (size_t)nq * BulkRows<V>::CRB * sizeof(V);
 }
 
+// Thread 0: rows [c0, c1) of q_0..q_{nq-1} (rounded out to 16 bytes) into
+// buffer b of Qb ([2][nq][CRB]), completing on bar[b].
+template <typename V>
+__device__ __forceinline__ void bulk_issue_chunk(const LzArgs<V>& a, V* Qb, uint64_t* bar, int nq,
+                                                 int b, int c0, int c1) {
+  constexpr int AL = BulkRows<V>::AL, CRB = BulkRows<V>::CRB;
+  const int a0 = c0 & ~(AL - 1);
+  const int len = (c1 - a0 + AL - 1) / AL * AL;
+  const unsigned bytes = (unsigned)(len * sizeof(V));
+  V* dst = Qb + (size_t)b * nq * CRB;
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  mbar_expect_tx(&bar[b], bytes * (unsigned)nq);
+  for (int k = 0; k < nq; ++k)
+    bulk_g2s(dst + (size_t)k * CRB, a.Q + (long long)k * a.N + a0, bytes, &bar[b]);
+}
+
+// All threads: wait for chunk ci (buffer ci & 1); false (uniform) when the
+// copies did not complete in time, after flagging the grid error word and
+// draining this CTA's copies still in flight (chunks ci and ci + 1).
+__device__ __forceinline__ bool bulk_wait_chunk(uint64_t* bar, int ci, int nchunk, GridBar* gb) {
+  const bool ok = mbar_wait_bounded(&bar[ci & 1], (ci >> 1) & 1, 2000000000ull);
+  if (!__syncthreads_or(!ok)) return true;
+  if (threadIdx.x == 0) {
+    atomicExch(&gb->err, 1);
+    mbar_wait_bounded(&bar[ci & 1], (ci >> 1) & 1, 1000000000ull);
+    if (ci + 1 < nchunk)
+      mbar_wait_bounded(&bar[(ci + 1) & 1], ((ci + 1) >> 1) & 1, 1000000000ull);
+  }
+  __syncthreads();
+  return false;
+}
+
 template <typename V>
 __global__ void __launch_bounds__(RSB_BLOCK, 2) k_lz_bt(LzArgs<V> a, int j, GridBar* gb) {
   extern __shared__ __align__(128) unsigned char bt_sh[];
@@ -491,36 +523,16 @@ __global__ void __launch_bounds__(RSB_BLOCK, 2) k_lz_bt(LzArgs<V> a, int j, Grid
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   stage_coef<V, false>(u.c1, nc, u.isn, cv);  // ends with a CTA barrier
-  auto issue = [&](int ci) {  // thread 0: rows of chunk ci of q_0..q_j into buffer ci & 1
-    const int c0 = t.row0 + ci * RSB_BLOCK;
-    const int c1 = min(t.row1, c0 + RSB_BLOCK);
-    const int a0 = c0 & ~(AL - 1);
-    const int len = (c1 - a0 + AL - 1) / AL * AL;
-    const unsigned bytes = (unsigned)(len * sizeof(V));
-    uint64_t* b = &bar[ci & 1];
-    V* dst = Qb + (size_t)(ci & 1) * nq * CRB;
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    mbar_expect_tx(b, bytes * (unsigned)nq);
-    for (int k = 0; k < nq; ++k)
-      bulk_g2s(dst + (size_t)k * CRB, a.Q + (long long)k * a.N + a0, bytes, b);
-  };
-  if (threadIdx.x == 0) issue(0);
+  if (threadIdx.x == 0) bulk_issue_chunk(a, Qb, bar, nq, 0, t.row0, min(t.row1, t.row0 + RSB_BLOCK));
   Acc<V> acc[MAXCW];
   unsigned long long pbytes = 0;
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   for (int ci = 0; ci < nchunk; ++ci) {
-    if (threadIdx.x == 0 && ci + 1 < nchunk) issue(ci + 1);
-    const bool ok = mbar_wait_bounded(&bar[ci & 1], (ci >> 1) & 1, 2000000000ull);
-    if (__syncthreads_or(!ok)) {
-      // copies that never completed: flag, drain what is still in flight, stop
-      if (threadIdx.x == 0) {
-        atomicExch(&gb->err, 1);
-        mbar_wait_bounded(&bar[ci & 1], (ci >> 1) & 1, 1000000000ull);
-        if (ci + 1 < nchunk) mbar_wait_bounded(&bar[(ci + 1) & 1], ((ci + 1) >> 1) & 1, 1000000000ull);
-      }
-      __syncthreads();
-      return;
+    if (threadIdx.x == 0 && ci + 1 < nchunk) {
+      const int n0 = t.row0 + (ci + 1) * RSB_BLOCK;
+      bulk_issue_chunk(a, Qb, bar, nq, (ci + 1) & 1, n0, min(t.row1, n0 + RSB_BLOCK));
     }
+    if (!bulk_wait_chunk(bar, ci, nchunk, gb)) return;
     const int c0 = t.row0 + ci * RSB_BLOCK;
     const int c1 = min(t.row1, c0 + RSB_BLOCK);
     const V* Qc = Qb + (size_t)(ci & 1) * nq * CRB + (c0 - (c0 & ~(AL - 1)));
@@ -1519,9 +1531,10 @@ static int lanczos_run(const LevelGraph& G, const Tile* tiles, int ntiles, Unit*
   }
   // the staged step B (FP32) needs up to 2 * M * (RSB_BLOCK + 4) floats of
   // dynamic shared memory (83 KB at M = 40)
-  if (sizeof(V) == 4)
+  if (sizeof(V) == 4) {
     RSB_CK(cudaFuncSetAttribute(k_lz_bt<V>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)lz_bt_smem<V>(M)));
+  }
   cudaGraphExec_t exec = nullptr;
   std::vector<int> cap_pairs;
   if (use_graph) {
