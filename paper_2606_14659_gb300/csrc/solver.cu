@@ -605,6 +605,40 @@ struct JacShared {
 // T = double for the FP64 path; T = float for the mixed path, whose Lanczos
 // vectors are FP32 (so FP32-accurate Ritz vectors lose nothing) and whose
 // eigenvalue comes from the FP64 Rayleigh quotient at the end.
+// Rotation (c, s) of the symmetric 2x2 Schur step for (a_pp, a_qq, a_pq)
+// (Golub & Van Loan 8.5): t = sign(tau) / (|tau| + sqrt(1 + tau^2)) with
+// tau = (a_qq - a_pp) / (2 a_pq), c = 1 / sqrt(1 + t^2), s = t c.  The angle t
+// is taken in FP32 with fast division; c is normalised by Newton steps for
+// 1 / sqrt(x) (c <- c (3 - x c^2) / 2) in the working precision, so that
+// c^2 + s^2 = 1 to that precision.  Any t gives an orthogonal rotation; an
+// FP32-accurate t leaves a_pq at ~1e-7 of its size instead of zero, which the
+// following sweeps remove.  In FP64 this replaces two divisions and two square
+// roots, long dependent chains on GB300's FP64 pipe.
+// (an a_pq below FP32's range gives a non-finite angle: no rotation, t = 0)
+__device__ __forceinline__ float jac_tan(float app, float aqq, float apq) {
+  const float tau = __fdividef(aqq - app, 2.f * apq);
+  const float t = __fdividef(copysignf(1.f, tau), fabsf(tau) + sqrtf(fmaf(tau, tau, 1.f)));
+  return isfinite(t) ? t : 0.f;
+}
+__device__ __forceinline__ void jac_rotation(float app, float aqq, float apq, float& c, float& s) {
+  const float t = jac_tan(app, aqq, apq);
+  const float x = fmaf(t, t, 1.f);
+  float r = rsqrtf(x);
+  r = r * fmaf(-0.5f * x, r * r, 1.5f);
+  c = r;
+  s = t * r;
+}
+__device__ __forceinline__ void jac_rotation(double app, double aqq, double apq, double& c,
+                                             double& s) {
+  const double t = (double)jac_tan(0.f, (float)(aqq - app), (float)apq);
+  const double x = fma(t, t, 1.0);
+  double r = (double)rsqrtf((float)x);
+  r = r * fma(-0.5 * x, r * r, 1.5);
+  r = r * fma(-0.5 * x, r * r, 1.5);
+  c = r;
+  s = t * r;
+}
+
 // tasks per thread and round: np*np + np*n2 <= 20*20 + 20*40 over RSB_BLOCK threads
 #define EIG_TASKS ((RSB_MAXM * RSB_MAXM * 3 / 4 + RSB_BLOCK - 1) / RSB_BLOCK)
 
@@ -673,12 +707,7 @@ __device__ void lz_eig_u(Unit& u, double* Sm, JacShared<T>& J) {
         if (pa > pb) { const int tt = pa; pa = pb; pb = tt; }
         T cc = T(1), ss = T(0);
         const T apq = J.A[pa][pb];
-        if (pb < K && apq != T(0)) {
-          const T tau = (J.A[pb][pb] - J.A[pa][pa]) / (T(2) * apq);
-          const T tt = (tau >= T(0) ? T(1) : T(-1)) / (fabs(tau) + sqrt(T(1) + tau * tau));
-          cc = T(1) / sqrt(T(1) + tt * tt);
-          ss = tt * cc;
-        }
+        if (pb < K && apq != T(0)) jac_rotation(J.A[pa][pa], J.A[pb][pb], apq, cc, ss);
         J.p[tid] = pa;
         J.q[tid] = pb;
         J.c[tid] = cc;
