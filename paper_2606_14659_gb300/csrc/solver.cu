@@ -470,18 +470,23 @@ constexpr size_t lz_bt_smem(int nq) {
 
 // Thread 0: rows [c0, c1) of q_0..q_{nq-1} (rounded out to 16 bytes) into
 // buffer b of Qb ([2][nq][CRB]), completing on bar[b].
+// (extra, when given, is one more N-vector staged after q_{nq-1}; slots = nq
+// or nq + 1)
 template <typename V>
 __device__ __forceinline__ void bulk_issue_chunk(const LzArgs<V>& a, V* Qb, uint64_t* bar, int nq,
-                                                 int b, int c0, int c1) {
+                                                 int b, int c0, int c1,
+                                                 const V* extra = nullptr) {
   constexpr int AL = BulkRows<V>::AL, CRB = BulkRows<V>::CRB;
+  const int slots = nq + (extra ? 1 : 0);
   const int a0 = c0 & ~(AL - 1);
   const int len = (c1 - a0 + AL - 1) / AL * AL;
   const unsigned bytes = (unsigned)(len * sizeof(V));
-  V* dst = Qb + (size_t)b * nq * CRB;
+  V* dst = Qb + (size_t)b * slots * CRB;
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-  mbar_expect_tx(&bar[b], bytes * (unsigned)nq);
+  mbar_expect_tx(&bar[b], bytes * (unsigned)slots);
   for (int k = 0; k < nq; ++k)
     bulk_g2s(dst + (size_t)k * CRB, a.Q + (long long)k * a.N + a0, bytes, &bar[b]);
+  if (extra) bulk_g2s(dst + (size_t)nq * CRB, extra + a0, bytes, &bar[b]);
 }
 
 // All threads: wait for chunk ci (buffer ci & 1); false (uniform) when the
@@ -581,6 +586,101 @@ __global__ void __launch_bounds__(RSB_BLOCK, 2) k_lz_bt(LzArgs<V> a, int j, Grid
       const double v = u.c1[1 + nd + k] + out[1 + nd + k];
       Sm[k * RSB_MAXM + j] = v;
       Sm[j * RSB_MAXM + k] = v;
+    }
+  }
+}
+
+// Step A of the FP32 streaming path in two launches.  A1: w = L q_j and
+// q_j = src / beta for every row (all of a thread's rows' gathers in flight),
+// written to global memory.  A2: the first-pass dots [1, D, q_0..q_j]^T w with
+// q_0..q_j and w staged chunk by chunk in shared memory by bulk copies, as in
+// step B.  Together they compute what lz_a_t computes, in the same order.
+template <typename V>
+__global__ void __launch_bounds__(RSB_BLOCK) k_lz_a1(LzArgs<V> a, int j) {
+  __shared__ double scale;
+  const Tile t = a.tiles[blockIdx.x];
+  const Unit& u = a.units[t.unit];
+  if (u.status != U_ACTIVE || j >= u.msteps || j < u.j0) return;
+  if (threadIdx.x == 0) scale = 1.0 / (j == u.j0 ? u.beta0 : u.beta[j]);
+  __syncthreads();
+  const V s = V(scale);
+  const V* src = (j & 1) ? a.W1 : a.W0;
+  V* dst = (j & 1) ? a.W0 : a.W1;
+  V* qj = a.Q + (long long)j * a.N;
+  unsigned long long pbytes = 0;
+#pragma unroll 4
+  for (int r = t.row0 + threadIdx.x; r < t.row1; r += RSB_BLOCK) {
+    const V xr = src[r];
+    dst[r] = s * spmv_row<V, false>(a.slice_ptr, a.ent, src, r, xr);
+    qj[r] = s * xr;
+    if (a.pb_a) pbytes += 4ull * row_width(a.slice_ptr, r) + 3ull * sizeof(V);
+  }
+  if (a.pb_a) prof_add(a.pb_a, pbytes);
+}
+
+template <typename V>
+__global__ void __launch_bounds__(RSB_BLOCK, 2) k_lz_a2(LzArgs<V> a, int j, GridBar* gb) {
+  extern __shared__ __align__(128) unsigned char a2_sh[];
+  constexpr int AL = BulkRows<V>::AL, CRB = BulkRows<V>::CRB;
+  __shared__ __align__(8) uint64_t bar[2];
+  __shared__ double out[RSB_MAXC];
+  const Tile t = a.tiles[blockIdx.x];
+  Unit& u = a.units[t.unit];
+  if (u.status != U_ACTIVE || j >= u.msteps || j < u.j0) return;
+  V* Qb = reinterpret_cast<V*>(a2_sh);  // [2][j + 2][CRB]: q_0..q_j, then w
+  const int nd = u.nd;
+  const int nc = 2 + nd + j;
+  const int nq = j + 1;
+  const int slots = nq + 1;
+  const V* wsrc = (j & 1) ? a.W0 : a.W1;
+  const int nchunk = (t.row1 - t.row0 + RSB_BLOCK - 1) / RSB_BLOCK;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    bulk_issue_chunk(a, Qb, bar, nq, 0, t.row0, min(t.row1, t.row0 + RSB_BLOCK), wsrc);
+  }
+  __syncthreads();
+  Acc<V> acc[MAXCW];
+  unsigned long long pbytes = 0;
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int ci = 0; ci < nchunk; ++ci) {
+    if (threadIdx.x == 0 && ci + 1 < nchunk) {
+      const int n0 = t.row0 + (ci + 1) * RSB_BLOCK;
+      bulk_issue_chunk(a, Qb, bar, nq, (ci + 1) & 1, n0, min(t.row1, n0 + RSB_BLOCK), wsrc);
+    }
+    if (!bulk_wait_chunk(bar, ci, nchunk, gb)) return;
+    const int c0 = t.row0 + ci * RSB_BLOCK;
+    const int c1 = min(t.row1, c0 + RSB_BLOCK);
+    const V* Qc = Qb + (size_t)(ci & 1) * slots * CRB + (c0 - (c0 & ~(AL - 1)));
+    const V* ws = Qc + (size_t)nq * CRB;
+    const int nr = c1 - c0;
+    if (a.pb_a && (int)threadIdx.x < nr)
+      pbytes += sizeof(V) * (unsigned long long)(1 + j) + 8ull * nd;
+#pragma unroll
+    for (int i = 0; i < MAXCW; ++i) {
+      const int c = w + RSB_WARPS * i;
+      if (c < nc) {
+        if (c == 0) {
+          for (int rl = lane; rl < nr; rl += 32) acc[i].add(V(1) * ws[rl]);
+        } else if (c <= nd) {
+          const double* d = c == 1 ? a.D0 : a.D1;
+          for (int rl = lane; rl < nr; rl += 32) acc[i].add(V(d[c0 + rl]) * ws[rl]);
+        } else {
+          const V* q = Qc + (size_t)(c - 1 - nd) * CRB;
+          for (int rl = lane; rl < nr; rl += 32) acc[i].add(q[rl] * ws[rl]);
+        }
+      }
+    }
+    __syncthreads();
+  }
+  store_dots<V>(a, nc, acc, blockIdx.x);
+  if (a.pb_a) prof_add(a.pb_a, pbytes);
+  if (last_cta(&u.cnt, u.ntile)) {
+    final_reduce(a.partials, a.stride, u.tile0, u.ntile, nc, out);
+    if (threadIdx.x == 0) {
+      u.c1[0] = out[0] * u.isn;
+      for (int c = 1; c < nc; ++c) u.c1[c] = out[c];
     }
   }
 }
@@ -1460,8 +1560,15 @@ static int lz_cycle(LzArgs<V>& a, int ntiles, int nunits, int M, double breakdow
                     cudaStream_t s) {
   for (int j = 0; j < M; ++j) {
     int pi = prof_before(PROF_LZ_A, s);
-    k_lz_a<V><<<ntiles, RSB_BLOCK, 0, s>>>(a, j);
-    RSB_CKL("k_lz_a");
+    if (sizeof(V) == 4) {
+      k_lz_a1<V><<<ntiles, RSB_BLOCK, 0, s>>>(a, j);
+      RSB_CKL("k_lz_a1");
+      k_lz_a2<V><<<ntiles, RSB_BLOCK, lz_bt_smem<V>(j + 2), s>>>(a, j, gb);
+      RSB_CKL("k_lz_a2");
+    } else {
+      k_lz_a<V><<<ntiles, RSB_BLOCK, 0, s>>>(a, j);
+      RSB_CKL("k_lz_a");
+    }
     prof_after(pi, s);
     pi = prof_before(PROF_LZ_B, s);
     if (sizeof(V) == 4) {  // FP32: bandwidth-bound, basis staged by bulk copies
@@ -1563,6 +1670,8 @@ static int lanczos_run(const LevelGraph& G, const Tile* tiles, int ntiles, Unit*
   if (sizeof(V) == 4) {
     RSB_CK(cudaFuncSetAttribute(k_lz_bt<V>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)lz_bt_smem<V>(M)));
+    RSB_CK(cudaFuncSetAttribute(k_lz_a2<V>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)lz_bt_smem<V>(M + 1)));
   }
   cudaGraphExec_t exec = nullptr;
   std::vector<int> cap_pairs;
@@ -1587,7 +1696,7 @@ static int lanczos_run(const LevelGraph& G, const Tile* tiles, int ntiles, Unit*
   for (int cyc = 0; cyc < 100000; ++cyc) {
     if (exec) {
       cudaError_t e = cudaGraphLaunch(exec, s);
-      rsb_count_launch(3 * M + 3);
+      rsb_count_launch((sizeof(V) == 4 ? 4 : 3) * M + 5);  // the kernels of one cycle
       if (e != cudaSuccess) {
         cudaGraphExecDestroy(exec);
         return rsb_set_cuda_error(e, "cudaGraphLaunch");
