@@ -222,6 +222,16 @@ int rsb_laplacian_bench(const rsb_csr *g, int f32, int reps, double *ms_per_appl
                         double *useful_bytes, void *stream);
 
 /*
+ * Failure-path test hook (not part of the method).  While on != 0, the
+ * persistent launch modes (use_graph 2 and 3) start their grid barrier from a
+ * corrupted arrival count, so no CTA sees the last arrival: every bounded wait
+ * runs out (4 s of the GPU's global timer), the kernel ends, and the call
+ * returns RSB_ETIMEOUT.  Nothing faults or hangs; the next call with the hook
+ * off starts from a clean barrier.  Process-wide, not thread-safe; for tests.
+ */
+void rsb_test_poison_barrier(int on);
+
+/*
  * rsb_laplacian_apply_noalloc — y = L x (FP64) like rsb_laplacian_apply, for
  * callers that cannot allocate device memory.  The paper has no counterpart;
  * this is a deployment variant.  Some callers must not call cudaMalloc: code

@@ -1325,6 +1325,8 @@ extern "C" int rsb_laplacian_bench(const rsb_csr* g, int f32, int reps, double* 
   return lap_common(g, nullptr, nullptr, f32 ? 1 : 0, reps, ms_per_apply, useful_bytes, stream);
 }
 
+extern "C" void rsb_test_poison_barrier(int on) { g_rsb_poison_barrier = on ? 1 : 0; }
+
 extern "C" const char* rsb_strerror(int code) {
   switch (code) {
     case RSB_OK: return "success";

@@ -280,6 +280,9 @@ struct GridBar {
   int pad;
 };
 
+// Test hook of the failure path (set by rsb_test_poison_barrier).
+extern int g_rsb_poison_barrier;
+
 __device__ __forceinline__ unsigned long long global_ns() {
   unsigned long long t;
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));

@@ -30,6 +30,8 @@
 
 #include "rsb_internal.cuh"
 
+int g_rsb_poison_barrier = 0;  // test hook, see rsb_test_poison_barrier
+
 template <typename V>
 struct LzArgs {
   const int64_t* slice_ptr;
@@ -1611,6 +1613,13 @@ static int lanczos_run(const LevelGraph& G, const Tile* tiles, int ntiles, Unit*
   rc = lz_start<V>(a, ntiles, sd, from64, from32, s);
   if (rc) return rc;
   const double breakdown = 1e-14;
+  if (B.gb) {
+    // a fresh barrier (count, generation, error word) for this solve; the
+    // failure-path test hook starts the count where no CTA sees the last arrival
+    RSB_CK(cudaMemsetAsync(B.gb, 0, sizeof(GridBar), s));
+    if (g_rsb_poison_barrier && (use_graph == 2 || use_graph == 3))
+      RSB_CK(cudaMemsetAsync(&B.gb->count, 0x40, sizeof(unsigned int), s));
+  }
   if (use_graph == 3 && B.gb && B.trmax > 0) {
     // the whole solve in one cooperative launch when every tile gets a
     // co-resident CTA holding its rows of the basis; otherwise CUDA graphs

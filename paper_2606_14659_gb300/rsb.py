@@ -24,7 +24,8 @@ RSB_DEGEN_NONE, RSB_DEGEN_RESOLVE = 0, 1
 EXPORTED = ["rsb_options_default", "rsb_partition", "rsb_partition_batch", "rsb_fiedler",
             "rsb_laplacian_apply", "rsb_laplacian_apply_f32", "rsb_laplacian_bench",
             "rsb_strerror", "rsb_last_error_detail", "rsb_release", "rsb_profile_begin",
-            "rsb_profile_end", "rsb_laplacian_apply_noalloc", "rsb_autotune"]
+            "rsb_profile_end", "rsb_laplacian_apply_noalloc", "rsb_autotune",
+            "rsb_test_poison_barrier"]
 
 RSB_TUNE_CANDIDATES = 6
 TUNE_CANDIDATES = [(2, 3), (4, 3), (8, 3), (2, 1), (4, 1), (8, 1)]  # (tile_rows, use_graph)
@@ -84,6 +85,8 @@ def load():
                                         C.POINTER(C.c_double), C.POINTER(C.c_double), vp]
     lib.rsb_autotune.argtypes = [C.POINTER(rsb_csr), C.c_int32, C.POINTER(C.c_int32),
                                  C.POINTER(rsb_options), C.POINTER(vp), C.POINTER(C.c_double), vp]
+    lib.rsb_test_poison_barrier.argtypes = [C.c_int]
+    lib.rsb_test_poison_barrier.restype = None
     lib.rsb_strerror.argtypes = [C.c_int]
     lib.rsb_strerror.restype = C.c_char_p
     lib.rsb_last_error_detail.argtypes = []
@@ -321,6 +324,11 @@ def rsb_laplacian_bench(g: Graph, f32: bool, reps: int = 20, stream=None):
     _check(lib.rsb_laplacian_bench(C.byref(cs), int(bool(f32)), int(reps), C.byref(ms),
                                    C.byref(by), _stream(stream)), "rsb_laplacian_bench")
     return ms.value, by.value
+
+
+def rsb_test_poison_barrier(on: bool):
+    """Failure-path test hook: the persistent launch modes' grid barrier times out."""
+    load().rsb_test_poison_barrier(1 if on else 0)
 
 
 def rsb_release():
