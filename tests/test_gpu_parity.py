@@ -228,6 +228,23 @@ def test_partition_random_vs_oracle(seed, P):
     assert np.mean(part == ref) > 0.95
 
 
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_graph_launch_partitions_equal_resident_on_unaligned_units(precision):
+    # an irregular mesh split 7 ways and a batch of odd-sized boxes: from the
+    # second level on, units start at arbitrary rows, so the bulk copies of the
+    # graph launch start inside a 16-byte group and end on ragged chunks; the
+    # staged kernels must reproduce the resident kernel bit for bit
+    g = box_graph_deleted(23, 17, 11, 0.07, 5, "vertex")
+    res = R.rsb_partition(R.graph(g), 7, R.options(precision=precision, use_graph=3))[0]
+    gra = R.rsb_partition(R.graph(g), 7, R.options(precision=precision, use_graph=1))[0]
+    assert np.array_equal(_np(res), _np(gra))
+    gs = [R.graph(box_graph(*d)) for d in [(7, 5, 3), (9, 13, 5), (11, 3, 7), (6, 6, 6)]]
+    res = R.rsb_partition_batch(gs, [5, 3, 6, 7], R.options(precision=precision, use_graph=3))[0]
+    gra = R.rsb_partition_batch(gs, [5, 3, 6, 7], R.options(precision=precision, use_graph=1))[0]
+    for a, b in zip(res, gra):
+        assert np.array_equal(_np(a), _np(b))
+
+
 def test_partition_disconnected_vs_oracle():
     g = disjoint_union([box_graph(4, 2, 1), box_graph(3, 2, 1), box_graph(5, 2, 1),
                         random_graph(9, 6, 3)])
