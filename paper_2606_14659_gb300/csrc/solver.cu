@@ -702,13 +702,6 @@ struct JacShared {
   int p[RSB_MAXM / 2], q[RSB_MAXM / 2];
   double red[RSB_WARPS];
   int rank[RSB_MAXM];
-  // tridiagonal route (FP32): T = Q^T S Q, eigenvalues, pivots, work vectors
-  T d[RSB_MAXM], e[RSB_MAXM], tau[RSB_MAXM];
-  T w[RSB_MAXKEEP + 1];
-  T piv[RSB_MAXKEEP + 1][RSB_MAXM];  // reciprocal LDL^T pivots of T - w_i I
-  T tmp[RSB_MAXM];
-  T sc[8];
-  int ok;
 };
 
 // T = double for the FP64 path; T = float for the mixed path, whose Lanczos
@@ -748,239 +741,6 @@ __device__ __forceinline__ void jac_rotation(double app, double aqq, double apq,
   s = t * r;
 }
 
-// ----------------------------------------------------------------------------
-// The ne smallest eigenpairs of S (n x n) in FP32 by the tridiagonal route, in
-// far fewer dependent rounds than Jacobi (Golub & Van Loan 8.3 and 8.4):
-//  1. Householder reduction S = Q T Q^T (n - 2 reflections H_k = I - tau_k v_k
-//     v_k^T, each a norm, a matrix-vector product and a rank-2 update);
-//  2. eigenvalue i of T by multisection on Sturm counts (one warp per
-//     eigenvalue, 32 trial shifts per round);
-//  3. eigenvectors of T by inverse iteration on the LDL^T factorisation of
-//     T - w_i I (pivots kept away from zero by 1e-6 ||T||), then modified
-//     Gram-Schmidt over all of them (clustered eigenvalues give nearly
-//     parallel iterates; near-clusters leave 1e-5-size overlaps otherwise);
-//  4. u_i = Q z_i by the stored reflections.
-// The result is checked against S itself (||S u_i - w_i u_i|| and u_i^T u_j);
-// false sends the caller to the Jacobi solve.  On success J.w[0..ne) holds the
-// eigenvalues ascending and J.Z[l][i] component l of eigenvector i.
-// ----------------------------------------------------------------------------
-__device__ __forceinline__ float warp_sum_f(float v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
-}
-
-template <bool CO>
-__device__ bool eig_tri_f32(const double* Sm, int n, int ne, JacShared<float>& J) {
-  const int tid = threadIdx.x, lane = tid & 31, wp = tid >> 5;
-  for (int idx = tid; idx < n * n; idx += RSB_BLOCK)
-    J.A[idx / n][idx % n] = (float)ldc<CO>(Sm + (idx / n) * RSB_MAXM + idx % n);
-  __syncthreads();
-  // 1. Householder: column k below the diagonal becomes mu e_1
-  for (int k = 0; k + 2 < n; ++k) {
-    const int m = n - k - 1;
-    if (wp == 0) {
-      float sg = 0.f;
-      for (int i = 1 + lane; i < m; i += 32) sg = fmaf(J.A[k + 1 + i][k], J.A[k + 1 + i][k], sg);
-      sg = warp_sum_f(sg);
-      if (lane == 0) {
-        const float x0 = J.A[k + 1][k];
-        float beta = 0.f, v1 = 1.f;
-        if (sg > 0.f) {
-          const float mu = sqrtf(fmaf(x0, x0, sg));
-          v1 = x0 <= 0.f ? x0 - mu : -sg / (x0 + mu);
-          beta = 2.f * v1 * v1 / (sg + v1 * v1);
-          J.e[k] = mu;
-        } else {
-          J.e[k] = x0;
-        }
-        J.tau[k] = beta;
-        J.sc[0] = v1;
-      }
-    }
-    __syncthreads();
-    const float beta = J.tau[k];
-    if (beta == 0.f) continue;  // uniform: read from shared memory
-    const float v1 = J.sc[0];
-    for (int i = tid; i < m; i += RSB_BLOCK) J.A[k + 1 + i][k] = i == 0 ? 1.f : J.A[k + 1 + i][k] / v1;
-    __syncthreads();
-    for (int i = tid >> 3; i < ((m + 31) & ~31); i += RSB_BLOCK / 8) {  // p = beta A22 v, 8 lanes a row
-      float acc = 0.f;
-      if (i < m)
-        for (int jj = tid & 7; jj < m; jj += 8)
-          acc = fmaf(J.A[k + 1 + i][k + 1 + jj], J.A[k + 1 + jj][k], acc);
-      acc += __shfl_xor_sync(0xffffffffu, acc, 4);
-      acc += __shfl_xor_sync(0xffffffffu, acc, 2);
-      acc += __shfl_xor_sync(0xffffffffu, acc, 1);
-      if (i < m && (tid & 7) == 0) J.tmp[i] = beta * acc;
-    }
-    __syncthreads();
-    if (wp == 0) {  // gamma = beta / 2 p^T v
-      float g = 0.f;
-      for (int i = lane; i < m; i += 32) g = fmaf(J.tmp[i], J.A[k + 1 + i][k], g);
-      g = warp_sum_f(g);
-      if (lane == 0) J.sc[1] = 0.5f * beta * g;
-    }
-    __syncthreads();
-    const float gam = J.sc[1];
-    for (int i = tid; i < m; i += RSB_BLOCK) J.tmp[i] = fmaf(-gam, J.A[k + 1 + i][k], J.tmp[i]);
-    __syncthreads();
-    for (int idx = tid; idx < m * m; idx += RSB_BLOCK) {  // A22 -= v w^T + w v^T
-      const int i = idx / m, jj = idx - i * m;
-      J.A[k + 1 + i][k + 1 + jj] -=
-          J.A[k + 1 + i][k] * J.tmp[jj] + J.tmp[i] * J.A[k + 1 + jj][k];
-    }
-    __syncthreads();
-  }
-  if (tid < n) J.d[tid] = J.A[tid][tid];
-  if (tid == 0) {
-    if (n >= 2) J.e[n - 2] = J.A[n - 1][n - 2];
-    float lo = 3.4e38f, hi = -3.4e38f, e2 = 0.f;
-    for (int i = 0; i < n; ++i) {
-      const float r = (i > 0 ? fabsf(J.e[i - 1]) : 0.f) + (i + 1 < n ? fabsf(J.e[i]) : 0.f);
-      lo = fminf(lo, J.d[i] - r);
-      hi = fmaxf(hi, J.d[i] + r);
-      if (i + 1 < n) e2 = fmaxf(e2, J.e[i] * J.e[i]);
-    }
-    const float tn = fmaxf(fmaxf(fabsf(lo), fabsf(hi)), 1e-30f);
-    J.sc[2] = lo - 1e-6f * tn;
-    J.sc[3] = hi + 1e-6f * tn;
-    J.sc[4] = tn;
-    J.sc[5] = 1e-36f * fmaxf(1.f, e2);  // pivot floor of the Sturm counts
-  }
-  __syncthreads();
-  const float tn = J.sc[4], pivmin = J.sc[5];
-  // 2. eigenvalue ii of T: the 32 lanes place trial shifts, the bracket shrinks 33-fold
-  for (int ii = wp; ii < ne; ii += RSB_WARPS) {
-    float a = J.sc[2], b = J.sc[3];
-    for (int it = 0; it < 12; ++it) {
-      const float x = a + (b - a) * (float)(lane + 1) / 33.f;
-      float q = J.d[0] - x;
-      if (fabsf(q) < pivmin) q = -pivmin;
-      int cnt = q < 0.f;
-      for (int i = 1; i < n; ++i) {  // only the pivots' signs count: fast division
-        q = J.d[i] - x - __fdividef(J.e[i - 1] * J.e[i - 1], q);
-        if (fabsf(q) < pivmin) q = -pivmin;
-        cnt += q < 0.f;
-      }
-      const unsigned above = __ballot_sync(0xffffffffu, cnt > ii);
-      const int ls = above ? __ffs(above) - 1 : 32;
-      const float na = ls == 0 ? a : a + (b - a) * (float)ls / 33.f;
-      const float nb = ls == 32 ? b : a + (b - a) * (float)(ls + 1) / 33.f;
-      a = na;
-      b = nb;
-      if (b - a <= 2.4e-7f * fmaxf(fabsf(a), fabsf(b)) + 1e-30f) break;
-    }
-    if (lane == 0) J.w[ii] = 0.5f * (a + b);
-  }
-  __syncthreads();
-  // 3. inverse iteration, one thread per eigenvalue; then Gram-Schmidt
-  const float floor_ = 1e-6f * tn;
-  for (int round = 0; round < 2; ++round) {
-    if (tid < ne) {
-      const int i = tid;
-      const float th = J.w[i];
-      if (round == 0) {
-        float Dp = J.d[0] - th;
-        if (fabsf(Dp) < floor_) Dp = Dp < 0.f ? -floor_ : floor_;
-        float rD = 1.f / Dp;
-        J.piv[i][0] = rD;  // reciprocal pivots
-        for (int l = 1; l < n; ++l) {
-          float D = J.d[l] - th - J.e[l - 1] * J.e[l - 1] * rD;
-          if (fabsf(D) < floor_) D = D < 0.f ? -floor_ : floor_;
-          rD = 1.f / D;
-          J.piv[i][l] = rD;
-        }
-        for (int l = 0; l < n; ++l) J.Z[l][i] = (l & 1) ? 0.7f : 1.f;  // start vector
-      }
-      for (int step = 0; step < (round == 0 ? 2 : 1); ++step) {
-        float y = J.Z[0][i];  // forward: L y = b  (L = 1 + e / D below the diagonal)
-        for (int l = 1; l < n; ++l) {
-          y = fmaf(-J.e[l - 1] * J.piv[i][l - 1], y, J.Z[l][i]);
-          J.Z[l][i] = y;
-        }
-        float x = J.Z[n - 1][i] * J.piv[i][n - 1];  // D z = y, L^T x = z
-        J.Z[n - 1][i] = x;
-        float mx = fabsf(x);
-        for (int l = n - 2; l >= 0; --l) {
-          x = (J.Z[l][i] - J.e[l] * x) * J.piv[i][l];
-          J.Z[l][i] = x;
-          mx = fmaxf(mx, fabsf(x));
-        }
-        float nrm = 0.f;
-        const float sc = 1.f / fmaxf(mx, 1e-30f);
-        for (int l = 0; l < n; ++l) {
-          const float v = J.Z[l][i] * sc;
-          J.Z[l][i] = v;
-          nrm = fmaf(v, v, nrm);
-        }
-        const float rn = rsqrtf(nrm);
-        for (int l = 0; l < n; ++l) J.Z[l][i] *= rn;
-      }
-    }
-    __syncthreads();
-    if (wp == 0) {  // modified Gram-Schmidt, in eigenvalue order
-      for (int i = 1; i < ne; ++i) {
-        bool touched = false;
-        for (int jv = 0; jv < i; ++jv) {
-          float dt = 0.f;
-          for (int l = lane; l < n; l += 32) dt = fmaf(J.Z[l][jv], J.Z[l][i], dt);
-          dt = warp_sum_f(dt);
-          for (int l = lane; l < n; l += 32) J.Z[l][i] = fmaf(-dt, J.Z[l][jv], J.Z[l][i]);
-          __syncwarp();
-          touched = true;
-        }
-        if (touched) {
-          float nr = 0.f;
-          for (int l = lane; l < n; l += 32) nr = fmaf(J.Z[l][i], J.Z[l][i], nr);
-          nr = warp_sum_f(nr);
-          const float rn = nr > 0.f ? rsqrtf(nr) : 0.f;
-          for (int l = lane; l < n; l += 32) J.Z[l][i] *= rn;
-          __syncwarp();
-        }
-      }
-    }
-    __syncthreads();
-  }
-  // 4. u_i = H_0 (H_1 (... H_{n-3} z_i)), warp per eigenvector
-  for (int i = wp; i < ne; i += RSB_WARPS) {
-    for (int k = n - 3; k >= 0; --k) {
-      const float tk = J.tau[k];
-      if (tk == 0.f) continue;
-      float dt = 0.f;
-      for (int r = k + 1 + lane; r < n; r += 32)
-        dt = fmaf(r == k + 1 ? 1.f : J.A[r][k], J.Z[r][i], dt);
-      dt = warp_sum_f(dt) * tk;
-      for (int r = k + 1 + lane; r < n; r += 32)
-        J.Z[r][i] = fmaf(-dt, r == k + 1 ? 1.f : J.A[r][k], J.Z[r][i]);
-      __syncwarp();
-    }
-  }
-  if (tid == 0) J.ok = 1;
-  __syncthreads();
-  // check against S: residual and orthonormality
-  for (int i = wp; i < ne; i += RSB_WARPS) {
-    float r2 = 0.f;
-    for (int l = lane; l < n; l += 32) {
-      float acc = -J.w[i] * J.Z[l][i];
-      for (int mcol = 0; mcol < n; ++mcol)
-        acc = fmaf((float)ldc<CO>(Sm + l * RSB_MAXM + mcol), J.Z[mcol][i], acc);
-      r2 = fmaf(acc, acc, r2);
-    }
-    r2 = warp_sum_f(r2);
-    bool good = r2 <= (1e-5f * tn) * (1e-5f * tn) && r2 == r2;
-    for (int jv = 0; jv <= i; ++jv) {
-      float dt = 0.f;
-      for (int l = lane; l < n; l += 32) dt = fmaf(J.Z[l][jv], J.Z[l][i], dt);
-      dt = warp_sum_f(dt);
-      good = good && fabsf(dt - (jv == i ? 1.f : 0.f)) <= 1e-5f;
-    }
-    if (lane == 0 && !good) J.ok = 0;
-  }
-  __syncthreads();
-  return J.ok != 0;
-}
-
 // tasks per thread and round: np*np + np*n2 <= 20*20 + 20*40 over RSB_BLOCK threads
 #define EIG_TASKS ((RSB_MAXM * RSB_MAXM * 3 / 4 + RSB_BLOCK - 1) / RSB_BLOCK)
 
@@ -989,23 +749,6 @@ __device__ void lz_eig_u(Unit& u, double* Sm, JacShared<T>& J) {
   if (ldc<CO>(&u.status) != U_ACTIVE) return;
   const int tid = threadIdx.x;
   const int K = ldc<CO>(&u.msteps);
-  if constexpr (sizeof(T) == 4) {
-    const int kk0 = ldc<CO>(&u.broke) ? 0 : min(u.keep, K - 1);
-    if (K >= 3 && eig_tri_f32<CO>(Sm, K, kk0 + 1, J)) {
-      double* Ym = Sm + RSB_MAXM * RSB_MAXM;
-      for (int idx = tid; idx < K * (kk0 + 1); idx += RSB_BLOCK) {
-        const int l = idx / (kk0 + 1), i = idx % (kk0 + 1);
-        Ym[l * RSB_MAXM + i] = (double)J.Z[l][i];
-      }
-      if (tid <= kk0) u.th[tid] = (double)J.w[tid];
-      if (tid == 0) {
-        u.theta = (double)J.w[0];
-        u.kk = kk0;
-      }
-      __syncthreads();
-      return;
-    }
-  }
   const int n2 = K + (K & 1);
   for (int idx = tid; idx < n2 * n2; idx += RSB_BLOCK) {
     const int i = idx / n2, k = idx % n2;
