@@ -126,21 +126,6 @@ typedef struct rsb_stats {
 void rsb_options_default(rsb_options *o);
 
 /*
- * Kernel timing for bandwidth accounting (not part of the method).
- * rsb_profile_begin(family) makes the following calls bracket every launch of
- * one kernel family with CUDA events on the library's stream and add up the
- * algorithmic bytes of each launch; rsb_profile_end() returns the totals and
- * switches timing off.  family: 1 Lanczos step A (SpMV + first Gram-Schmidt
- * dots), 2 step B (update + second dots), 3 step C (update + norm), 4 CG
- * Laplacian action, 5 Laplacian action of rsb_laplacian_bench, 6 the
- * persistent Lanczos-cycle kernel (bytes of its A, B and C phases).
- * Bytes count 4 B per stored SELL entry (padding included), every vector
- * element read or written once, and FP64 deflation vectors.
- */
-void rsb_profile_begin(int family);
-void rsb_profile_end(double *ms_total, int64_t *launches, double *bytes_total);
-
-/*
  * Recursive spectral bisection of one graph into nparts parts (§4,
  * Algorithm 1; sizes per §4: a segment of parts [p0, p1) holds
  * floor(p1 n / P) - floor(p0 n / P) elements and its left child gets the
@@ -222,16 +207,6 @@ int rsb_laplacian_bench(const rsb_csr *g, int f32, int reps, double *ms_per_appl
                         double *useful_bytes, void *stream);
 
 /*
- * Failure-path test hook (not part of the method).  While on != 0, the
- * persistent launch modes (use_graph 2 and 3) start their grid barrier from a
- * corrupted arrival count, so no CTA sees the last arrival: every bounded wait
- * runs out (4 s of the GPU's global timer), the kernel ends, and the call
- * returns RSB_ETIMEOUT.  Nothing faults or hangs; the next call with the hook
- * off starts from a clean barrier.  Process-wide, not thread-safe; for tests.
- */
-void rsb_test_poison_barrier(int on);
-
-/*
  * rsb_laplacian_apply_noalloc — y = L x (FP64) like rsb_laplacian_apply, for
  * callers that cannot allocate device memory.  The paper has no counterpart;
  * this is a deployment variant.  Some callers must not call cudaMalloc: code
@@ -243,13 +218,14 @@ void rsb_test_poison_barrier(int on);
  * every GPU that loads the library holds until the process exits.
  *   g, x, y  device pointers only (RSB_EINVAL otherwise); x, y double[n]
  *   stream   used directly; the call returns after the result is on it
- * Graphs whose scratch exceeds the 32 MiB (about 4 B per padded SELL entry
- * plus 28 B per row) are rejected with RSB_EINVAL.  All calls share the array
+ * Graphs whose scratch exceeds the 32 MiB (4 B per padded SELL entry plus
+ * about 5 B per row) are rejected with RSB_EINVAL.  All calls share the array
  * and leave their contents in it; each call clears what must start at zero.
  * Calls that overlap on the GPU (other streams or host threads) race on the
- * array: order them.  The first call on each device looks up the array's
- * device address (cudaGetSymbolAddress, that device current); make it before
- * any stream capture.
+ * array: order them.  Every call reads the entry count back to the host and
+ * synchronises `stream`, so it cannot be used inside a stream capture.  The
+ * first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress, with that device current) and caches it.
  */
 int rsb_laplacian_apply_noalloc(const rsb_csr *g, const double *x, double *y, void *stream);
 

@@ -1,0 +1,45 @@
+/*
+ * rsb_test.h — measurement and test hooks of librsb.  They are not part of the
+ * method and not needed to partition a mesh: kernel timing for the bandwidth
+ * roofline of the benchmark, and a switch that drives the failure path of the
+ * bounded device waits in tests.  The method's calls are in rsb.h.
+ */
+#ifndef RSB_TEST_H
+#define RSB_TEST_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/*
+ * Kernel timing for bandwidth accounting (not part of the method).
+ * rsb_profile_begin(family) makes the following calls bracket every launch of
+ * one kernel family with CUDA events on the library's stream and add up the
+ * algorithmic bytes of each launch; rsb_profile_end() returns the totals and
+ * switches timing off.  family: 1 Lanczos step A (SpMV + first Gram-Schmidt
+ * dots), 2 step B (update + second dots), 3 step C (update + norm), 4 CG
+ * Laplacian action, 5 Laplacian action of rsb_laplacian_bench, 6 the
+ * persistent Lanczos-cycle kernel (bytes of its A, B and C phases).
+ * Bytes count 4 B per stored SELL entry (padding included), every vector
+ * element read or written once, and FP64 deflation vectors.
+ */
+void rsb_profile_begin(int family);
+void rsb_profile_end(double *ms_total, int64_t *launches, double *bytes_total);
+
+/*
+ * Failure-path test hook (not part of the method).  While on != 0, the
+ * persistent launch modes (use_graph 2 and 3) start their grid barrier from a
+ * corrupted arrival count, so no CTA sees the last arrival: every bounded wait
+ * runs out (4 s of the GPU's global timer), the kernel ends, and the call
+ * returns RSB_ETIMEOUT.  Nothing faults or hangs; the next call with the hook
+ * off starts from a clean barrier.  Process-wide, not thread-safe; for tests.
+ */
+void rsb_test_poison_barrier(int on);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RSB_TEST_H */

@@ -134,19 +134,27 @@ def degree(g) -> np.ndarray:
     return np.bincount(rows_of(g), weights=g.w.astype(np.float64), minlength=g.n)
 
 
+def adjacency_csr(g):
+    """The weighted adjacency A as a scipy CSR matrix (cached on the graph)."""
+    import scipy.sparse as sp
+
+    a = getattr(g, "_oracle_A", None)
+    if a is None or a.shape[0] != g.n or a.nnz != len(g.col):
+        a = sp.csr_matrix((g.w.astype(np.float64), np.asarray(g.col, dtype=np.int64),
+                           np.asarray(g.row_ptr, dtype=np.int64)), shape=(g.n, g.n))
+        g._oracle_A = a
+    return a
+
+
 def laplacian_apply(g, x: np.ndarray) -> np.ndarray:
-    """y = (D - A) x with the assembled (CSR) Laplacian (§5, first option)."""
+    """y = (D - A) x with the assembled (CSR) Laplacian (§5, first option); the
+    product A x is the library's sparse matrix-vector product."""
     x = np.asarray(x, dtype=np.float64)
     d = getattr(g, "_oracle_deg", None)
     if d is None or len(d) != g.n:
         d = degree(g)
         g._oracle_deg = d
-    wf = getattr(g, "_oracle_wf", None)
-    if wf is None or len(wf) != len(g.w):
-        wf = g.w.astype(np.float64)
-        g._oracle_wf = wf
-    ax = np.bincount(rows_of(g), weights=wf * x[g.col], minlength=g.n)
-    return d * x - ax
+    return d * x - adjacency_csr(g) @ x
 
 
 def laplacian_dense(g) -> np.ndarray:
@@ -282,21 +290,6 @@ def _project_start(B, x):
     return x / np.linalg.norm(x)
 
 
-def tridiag_min_eigpair(alpha, beta):
-    """Smallest eigenpair of the symmetric tridiagonal T(alpha, beta) (§6).
-
-    alpha: diagonal (k); beta: off-diagonal (k-1).  Library eigensolver on the
-    dense T (k <= 40).
-    """
-    k = len(alpha)
-    T = np.diag(np.asarray(alpha, dtype=np.float64))
-    if k > 1:
-        b = np.asarray(beta[:k - 1], dtype=np.float64)
-        T += np.diag(b, 1) + np.diag(b, -1)
-    lam, vec = np.linalg.eigh(T)
-    return float(lam[0]), vec[:, 0]
-
-
 def lanczos_fiedler(g, opts: Options, deflate=(), start=None):
     """Fiedler pair of a connected graph by thick-restarted Lanczos (§6, reading R3).
 
@@ -312,7 +305,10 @@ def lanczos_fiedler(g, opts: Options, deflate=(), start=None):
     nb = B.shape[1]
     dmax = float(degree(g).max())
     q = start_vector(g.gid, opts.seed, nd) if start is None else np.array(start, dtype=np.float64)
-    V = np.zeros((n, m))
+    # columns: the fixed basis [1/sqrt(n), deflation vectors], then q_0..q_{m-1}
+    BV = np.zeros((n, nb + m))
+    BV[:, :nb] = B
+    V = BV[:, nb:]
     S = np.zeros((m, m))
     V[:, 0] = _project_start(B, q)
     j0 = 0
@@ -321,7 +317,7 @@ def lanczos_fiedler(g, opts: Options, deflate=(), start=None):
         meff, w_last = m, None
         for j in range(j0, m):
             w = laplacian_apply(g, V[:, j])
-            basis = np.concatenate([B, V[:, :j + 1]], axis=1)
+            basis = BV[:, :nb + j + 1]
             w, c1 = _cgs(basis, w)
             w, c2 = _cgs(basis, w)
             col = (c1 + c2)[nb:]

@@ -31,7 +31,8 @@ def _stale(obj: str, src: str) -> bool:
     if not os.path.exists(obj):
         return True
     t = os.path.getmtime(obj)
-    deps = [src, os.path.join(CSRC, "rsb_internal.cuh"), os.path.join(INCLUDE, "rsb.h")]
+    deps = [src, os.path.join(CSRC, "rsb_internal.cuh"), os.path.join(INCLUDE, "rsb.h"),
+            os.path.join(INCLUDE, "rsb_test.h")]
     return any(os.path.getmtime(d) > t for d in deps)
 
 

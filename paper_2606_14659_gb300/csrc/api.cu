@@ -18,6 +18,8 @@
 //   4. both halves are compacted into the next level's graph (R2).
 #include <chrono>
 #include <cmath>
+#include <cstdarg>
+#include <cstdlib>
 #include <cstdio>
 #include <cstring>
 #include <string>
@@ -82,6 +84,30 @@ int rsb_set_error(int code, const std::string& what) {
   return code;
 }
 void rsb_count_launch(int k) { g_launches += k; }
+
+// ----------------------------------------------------------------------------
+// tracing: with RSB_TRACE=1 in the environment, every level and every solve
+// stage prints its wall time (the stream is synchronised at each mark, so a
+// traced run is slower; off by default)
+// ----------------------------------------------------------------------------
+static int trace_on() {
+  const char* e = getenv("RSB_TRACE");
+  return (e && *e && *e != '0') ? 1 : 0;
+}
+static std::chrono::steady_clock::time_point g_trace_t0;
+static void trace_mark(cudaStream_t s, const char* fmt, ...) {
+  if (!trace_on()) return;
+  cudaStreamSynchronize(s);
+  const auto now = std::chrono::steady_clock::now();
+  const double ms = std::chrono::duration<double, std::milli>(now - g_trace_t0).count();
+  g_trace_t0 = now;
+  char buf[256];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  fprintf(stderr, "[rsb] %9.3f ms  %s\n", ms, buf);
+}
 
 // ----------------------------------------------------------------------------
 // kernel timing (rsb_profile_begin / rsb_profile_end)
@@ -551,6 +577,8 @@ static int solve_candidate(Ctx& c, const LevelGraph& G, const Tile* tiles, int n
                         use_graph, c.s);
   }
   if (rc) return rc;
+  trace_mark(c.s, "cand %d stage 1 (%s %s): %d units, %d tiles", cand,
+             inverse ? "inverse" : "lanczos", mixed ? "fp32" : "fp64", nunits, ntiles);
   const void* stage1_vec = inverse ? B.X : B.Y;
   if (!mixed) {
     if ((rc = solver_write_vector(G, tiles, ntiles, units, ckey, B, 0, inverse, out, cand, 0,
@@ -571,6 +599,7 @@ static int solve_candidate(Ctx& c, const LevelGraph& G, const Tile* tiles, int n
       return rc;
     if ((rc = solver_write_vector(G, tiles, ntiles, units, ckey, B64, 0, 1, out, cand, 0, c.s)))
       return rc;
+    trace_mark(c.s, "cand %d fp64 rayleigh quotient", cand);
     if (o.polish_cycles > 0) {
       // stage 3: at most polish_cycles FP64 Lanczos cycles of polish_dim steps,
       // started from the FP32 vector, stopping early at tol; a unit keeps the
@@ -584,6 +613,7 @@ static int solve_candidate(Ctx& c, const LevelGraph& G, const Tile* tiles, int n
       if ((rc = solver_write_vector(G, tiles, ntiles, units, ckey, B64, 0, 0, out, cand, 1, c.s)))
         return rc;
       if ((rc = solver_keep_better(units, nunits, cand, tol1, c.s))) return rc;
+      trace_mark(c.s, "cand %d fp64 polish (<= %d cycles of %d)", cand, o.polish_cycles, Mp);
     }
   }
   // statistics
@@ -593,6 +623,9 @@ static int solve_candidate(Ctx& c, const LevelGraph& G, const Tile* tiles, int n
   Counters h;
   RSB_CK(cudaMemcpyAsync(&h, cn, sizeof(Counters), cudaMemcpyDeviceToHost, c.s));
   RSB_CK(cudaStreamSynchronize(c.s));
+  if (trace_on())
+    fprintf(stderr, "[rsb]               cand %d: %lld cycles, %d capped, resid_max %.3e\n", cand,
+            (long long)h.cycles, h.capped, h.resid_max);
   rs.solves += 1;
   rs.cycles += h.cycles;
   rs.nonconv += h.capped;
@@ -675,8 +708,11 @@ static inline int64_t fl(int64_t p, int64_t N, int64_t P) { return (p * N) / P; 
 static int run_rsb(Ctx& c, const std::vector<MeshIn>& meshes, const std::vector<int32_t>& nparts,
                    const rsb_options& o, int32_t* part_concat, rsb_stats* st) {
   LevelGraph G;
+  trace_mark(c.s, "call start");
   int rc = build_level0(c, meshes, o.validate, G);
   if (rc) return rc;
+  trace_mark(c.s, "level-0 ingest: %lld rows, %lld stored entries", (long long)G.n,
+             (long long)G.nent);
   const int64_t N = G.n;
   std::vector<SegHost> segs;
   int64_t off = 0;
@@ -710,6 +746,7 @@ static int run_rsb(Ctx& c, const std::vector<MeshIn>& meshes, const std::vector<
       if (s.p1 - s.p0 >= 2) any = true;
     if (!any) break;
     ++levels;
+    trace_mark(c.s, "level %d start: %d segments, %lld rows", level, nseg, (long long)G.n);
     // R6 split sizes and the next level's segment table
     std::vector<SegHost> next;
     std::vector<int64_t> h_row0(nseg), h_nleft(nseg);
@@ -822,7 +859,9 @@ static int run_rsb(Ctx& c, const std::vector<MeshIn>& meshes, const std::vector<
     }
     std::vector<Tile> htiles;
     make_tiles(hunits, htiles, o.tile_rows > 0 ? o.tile_rows : RSB_MINR);
+    trace_mark(c.s, "level %d components and units", level);
     if ((rc = split_units(c, G, hunits, htiles, o, rs))) return rc;
+    trace_mark(c.s, "level %d split (%d units)", level, (int)hunits.size());
     if (level == 0 && !hunits.empty()) {
       Unit u0;
       RSB_CK(cudaMemcpyAsync(&u0, dptr<Unit>(c.units), sizeof(Unit), cudaMemcpyDeviceToHost, c.s));
@@ -877,6 +916,7 @@ static int run_rsb(Ctx& c, const std::vector<MeshIn>& meshes, const std::vector<
                              dptr<int64_t>(c.slice_sz), c.scan_tmp.p, c.scan_tmp.cap, c.ent[nxt],
                              c.s)))
       return rc;
+    trace_mark(c.s, "level %d compaction", level);
     G = H;
     cur = nxt;
     segs.swap(next);

@@ -102,10 +102,11 @@ __global__ void k_fill_sell(const int64_t* __restrict__ row_ptr, const int32_t* 
     d += (int)w;
   }
   for (; k < width; ++k) ent[base + 32ll * k + lane] = (uint32_t)r;  // weight 0, own column
-  deg[r] = d;
-  gid[r] = gid_in ? gid_in[i] : i;
-  home[r] = home_off + i;
-  row_seg[r] = seg;
+  // the per-row arrays are optional (NULL: not wanted by the caller)
+  if (deg) deg[r] = d;
+  if (gid) gid[r] = gid_in ? gid_in[i] : i;
+  if (home) home[r] = home_off + i;
+  if (row_seg) row_seg[r] = seg;
 }
 
 int launch_fill_sell(const int64_t* row_ptr, const int32_t* col, const int32_t* wt,

@@ -20,9 +20,11 @@
 //     the caller;
 //   * inputs and outputs must be device pointers (host pointers would need a
 //     staging allocation) and the caller's stream is used directly;
+//   * the call reads the entry count and the validation flag back to the host
+//     and synchronises the caller's stream, so it cannot be issued inside a
+//     stream capture at all;
 //   * the first call on a device looks up the array's device address with
-//     cudaGetSymbolAddress (with that device current) and caches it; make
-//     that first call before any stream capture.
+//     cudaGetSymbolAddress (with that device current) and caches it.
 #include <string>
 
 #include "rsb_internal.cuh"
@@ -72,7 +74,8 @@ extern "C" int rsb_laplacian_apply_noalloc(const rsb_csr* g, const double* x, do
   RSB_CK(cudaMemcpyAsync(&nnz, g->row_ptr + n, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
   RSB_CK(cudaStreamSynchronize(s));
   if (nnz < 0 || (nnz > 0 && !g->col)) return rsb_set_error(RSB_EINVAL, "row_ptr / col");
-  // scratch layout: flag | len | slice_sz | scan tmp | slice_ptr | deg | gid | home | row_seg | ent
+  // scratch layout: flag | len | slice_sz | scan tmp | slice_ptr | ent (the
+  // Laplacian action needs no per-row degree, gid or segment arrays)
   size_t off = 0;
   int* flag = (int*)(base + off);
   off += 256;
@@ -85,14 +88,6 @@ extern "C" int rsb_laplacian_apply_noalloc(const rsb_csr* g, const double* x, do
   off += align256(scan_bytes);
   int64_t* slice_ptr = (int64_t*)(base + off);
   off += align256(sizeof(int64_t) * (size_t)(nsl + 2));
-  int32_t* deg = (int32_t*)(base + off);
-  off += align256(sizeof(int32_t) * (size_t)n);
-  int64_t* gid = (int64_t*)(base + off);
-  off += align256(sizeof(int64_t) * (size_t)n);
-  int64_t* home = (int64_t*)(base + off);
-  off += align256(sizeof(int64_t) * (size_t)n);
-  int32_t* row_seg = (int32_t*)(base + off);
-  off += align256(sizeof(int32_t) * (size_t)n);
   const size_t ent_off = off;
   // the entries need at least 4 B per stored entry; the exact padded count is
   // known after the slice scan and checked again below
@@ -118,10 +113,10 @@ extern "C" int rsb_laplacian_apply_noalloc(const rsb_csr* g, const double* x, do
   G.nslices = nsl;
   G.slice_ptr = slice_ptr;
   G.ent = (uint32_t*)(base + ent_off);
-  G.deg = deg;
-  G.gid = gid;
-  G.home = home;
-  G.row_seg = row_seg;
+  G.deg = nullptr;
+  G.gid = nullptr;
+  G.home = nullptr;
+  G.row_seg = nullptr;
   G.nent = total;
   if ((rc = launch_fill_sell(g->row_ptr, g->col, g->weight, g->gid, n, 0, 0, 0, G.slice_ptr,
                              G.ent, G.deg, G.gid, G.home, G.row_seg, s)))

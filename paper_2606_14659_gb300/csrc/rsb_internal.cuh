@@ -29,6 +29,7 @@
 #include <vector>
 
 #include "rsb.h"
+#include "rsb_test.h"
 
 #define RSB_BLOCK 256
 #define RSB_WARPS (RSB_BLOCK / 32)

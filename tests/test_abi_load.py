@@ -1,4 +1,5 @@
-"""The C-ABI library builds, loads and exports every symbol include/rsb.h declares.
+"""The C-ABI library builds, loads and exports every symbol include/*.h declares
+(rsb.h: the method's calls; rsb_test.h: measurement and test hooks).
 
 CPU only: no compute call is made here.
 """
@@ -11,17 +12,23 @@ import pytest
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
-def _declared():
-    src = open(os.path.join(ROOT, "include", "rsb.h")).read()
-    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"\b(rsb_[a-z0-9_]+)\s*\(", src)))
+def _declared(headers=None):
+    inc = os.path.join(ROOT, "include")
+    names = set()
+    for h in headers or sorted(f for f in os.listdir(inc) if f.endswith(".h")):
+        src = re.sub(r"/\*.*?\*/", "", open(os.path.join(inc, h)).read(), flags=re.S)
+        names |= set(re.findall(r"\b(rsb_[a-z0-9_]+)\s*\(", src))
+    return sorted(names)
 
 
 def test_header_declares_the_boundary():
-    names = _declared()
+    names = _declared(["rsb.h"])
     for n in ("rsb_partition", "rsb_partition_batch", "rsb_fiedler", "rsb_strerror",
               "rsb_options_default", "rsb_release", "rsb_laplacian_apply"):
         assert n in names
+    hooks = _declared(["rsb_test.h"])
+    assert set(hooks) == {"rsb_profile_begin", "rsb_profile_end", "rsb_test_poison_barrier"}
+    assert not set(hooks) & set(names)
 
 
 def test_library_exports_every_declared_symbol():

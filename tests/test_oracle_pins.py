@@ -154,22 +154,6 @@ def test_zero_multiplicity_is_component_count():
         off += h.n
 
 
-def test_tridiag_min_eigpair_closed_form():
-    for k in (1, 2, 7, 40):
-        a = np.full(k, 2.0)
-        b = np.full(k - 1, -1.0)
-        lam, t = O.tridiag_min_eigpair(a, b)
-        assert abs(lam - (2 - 2 * np.cos(np.pi / (k + 1)))) < 1e-13
-        ref = np.sin(np.pi * np.arange(1, k + 1) / (k + 1))
-        ref /= np.linalg.norm(ref)
-        assert min(np.abs(t - ref).max(), np.abs(t + ref).max()) < 1e-12
-    rng = np.random.default_rng(1)
-    a, b = rng.standard_normal(30), rng.random(29) + 0.1
-    T = np.diag(a) + np.diag(b, 1) + np.diag(b, -1)
-    lam, _ = O.jacobi_eigh(T)
-    assert abs(O.tridiag_min_eigpair(a, b)[0] - lam[0]) < 1e-12
-
-
 # ---------------------------------------------------------------- Fiedler solvers
 
 
@@ -222,28 +206,24 @@ def test_lanczos_inverse_agree_on_deleted_mesh():
     assert np.abs(a[1] - b[1]).max() < 1e-5
 
 
-def test_planted_solver_mistake_is_caught():
-    """A Lanczos that forgets the projection against 1 returns lambda = 0."""
+def test_planted_solver_mistake_is_caught(monkeypatch):
+    """A Lanczos whose fixed basis lacks the constant vector (the projection
+    v _|_ 1 of §4 forgotten) converges to the null vector, lambda = 0: the box
+    closed form catches it."""
     g = box_graph(9, 5, 3)
-    bad = O.Options(method="lanczos")
-    n = g.n
+    good = O.lanczos_fiedler(g, O.Options()).lam
+    assert abs(good - O.box_lambda2(9, 5, 3)) < 1e-10
+    import oracle.rsb_oracle as M
 
-    def lanczos_no_projection(g, opts):
-        # same recurrence, but the fixed basis lacks the constant vector
-        q = O.start_vector(g.gid, opts.seed)
-        q /= np.linalg.norm(q)
-        Q, al, be = [q], [], []
-        for j in range(min(40, n - 1)):
-            w = O.laplacian_apply(g, Q[j]) - (be[j - 1] * Q[j - 1] if j else 0)
-            S = np.stack(Q, 1)
-            w = w - S @ (S.T @ w)
-            al.append(float(Q[j] @ O.laplacian_apply(g, Q[j])))
-            w = w - S @ (S.T @ w)
-            be.append(float(np.linalg.norm(w)))
-            Q.append(w / be[-1])
-        return O.tridiag_min_eigpair(al, be)[0]
+    real = M._fixed_basis
 
-    assert abs(lanczos_no_projection(g, bad) - O.box_lambda2(9, 5, 3)) > 1e-3
+    def no_ones(n, deflate):
+        B = real(n, deflate)
+        return B[:, 1:] if B.shape[1] > 1 else np.zeros((n, 1))
+
+    monkeypatch.setattr(M, "_fixed_basis", no_ones)
+    bad = O.lanczos_fiedler(g, O.Options(max_restarts=3)).lam
+    assert abs(bad - O.box_lambda2(9, 5, 3)) > 1e-3
 
 
 # ---------------------------------------------------------------- split rules
@@ -315,6 +295,48 @@ def test_partition_spectral_and_bruteforce_bounds():
                    for c in itertools.combinations(range(12), 6))
         assert cut >= best
         assert cut >= lam * 6 * 6 / 12 - 1e-9          # cut >= lambda_2 |A||B| / n
+
+
+def test_partition_metrics_hand_counted():
+    """Neighbour counts and cuts of §8's quality metrics on partitions counted by hand."""
+    # 4x4x1 face grid cut into its four 2x2 quadrants: every quadrant shares
+    # faces with exactly two others (not the diagonal one); 4 + 4 unit edges cross
+    g = box_graph(4, 4, 1)
+    i, j = np.arange(16) % 4, np.arange(16) // 4
+    quad = ((i >= 2) + 2 * (j >= 2)).astype(np.int32)
+    m = O.partition_metrics(g, quad, 4)
+    assert (m["max_neighbours"], m["avg_neighbours"]) == (2, 2.0)
+    assert (m["edge_cut"], m["weighted_cut"]) == (8, 8)
+    assert m["sizes"].tolist() == [4, 4, 4, 4]
+    # vertex adjacency of the same grid: the diagonal quadrants touch at the
+    # centre, so each has three neighbours; 8 face edges (weight 2*2 = 4) and
+    # 10 diagonal edges (weight 2) cross a quadrant boundary
+    m = O.partition_metrics(box_graph(4, 4, 1, "vertex"), quad, 4)
+    assert (m["max_neighbours"], m["avg_neighbours"]) == (3, 3.0)
+    assert (m["edge_cut"], m["weighted_cut"]) == (18, 8 * 4 + 10 * 2)
+    # a path of six elements in three parts: the middle part has two neighbours
+    m = O.partition_metrics(box_graph(6, 1, 1), np.array([0, 0, 1, 1, 2, 2], np.int32), 3)
+    assert m["max_neighbours"] == 2 and abs(m["avg_neighbours"] - 4 / 3) < 1e-15
+    assert (m["edge_cut"], m["weighted_cut"]) == (2, 2)
+    # one part: no neighbours, nothing cut
+    m = O.partition_metrics(g, np.zeros(16, np.int32), 1)
+    assert (m["max_neighbours"], m["edge_cut"], m["weighted_cut"]) == (0, 0, 0)
+
+
+def test_planted_neighbour_count_mistake_is_caught(monkeypatch):
+    """Counting cut edges per part instead of distinct neighbouring parts fails the pin."""
+    import oracle.rsb_oracle as M
+
+    def per_edge(g, part, P):
+        r = M.rows_of(g)
+        diff = part[r] != part[g.col]
+        nbr = np.bincount(part[r][diff], minlength=P)
+        return {"max_neighbours": int(nbr.max()), "avg_neighbours": float(nbr.mean())}
+
+    g = box_graph(4, 4, 1)
+    i, j = np.arange(16) % 4, np.arange(16) // 4
+    quad = ((i >= 2) + 2 * (j >= 2)).astype(np.int32)
+    assert per_edge(g, quad, 4)["max_neighbours"] != 2
 
 
 # ---------------------------------------------------------------- whole recursion
