@@ -1,27 +1,36 @@
 """Benchmark: elements bisected per second of full recursive spectral bisection.
 
-Default workload: the 64x64x32 box hex mesh (131,072 elements), face-adjacency
-dual graph with unit weights, bisected to 64 parts (6 levels) by Lanczos in
-mixed precision (FP32 vectors, FP64 coefficients / tridiagonal / Rayleigh
-quotient), every level's subgraphs batched in one set of launches; the tile
-rows and the launch mode (3: one persistent cooperative kernel per solve with
-the basis in shared memory when the level fits; 1: one CUDA graph per cycle)
-are picked by rsb_autotune before the timed region (--launch fixes the mode
-instead).  A step is one full rsb_partition call from device-resident CSR to
-part ids.  metric = (sum over levels and split segments of their element
+Default workload (the largest single-GPU configuration): the 256^3 box hex mesh
+with a seeded 5 % of its elements deleted (largest connected component kept,
+15,938,356 elements), vertex-adjacency dual graph with weights 4/2/1 shared
+vertices (26 neighbours), bisected to 1024 parts (10 levels) by Lanczos in mixed
+precision (FP32 vectors and SpMV, FP64 Gram-Schmidt coefficients, projected
+matrix, Rayleigh quotient and polish); every level's subgraphs are batched in
+one set of launches, the tile rows and launch mode picked by rsb_autotune before
+the timed region.  A step is one full rsb_partition call from device-resident
+CSR to part ids.  metric = (sum over levels and split segments of their element
 count) / time.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+                    [--workload c1|c2|c3|c4|c5] [--precision mixed|fp64]
+                    [--forms fp64 fp64_plain spmv cpu]
+    python bench.py --case lanczos|spmv|partition ...   (small fixed cases for ncu)
 
-Under torchrun each rank runs the same workload on its own GPU (independent
-replicas, no collective on the data path); the value is all ranks' elements
-bisected divided by the slowest rank's time.
+Other workloads: c1 16x8x4 face box -> 8 parts; c2 64x64x32 face box -> 64;
+c3 192x128x96 box, 10 % deleted, vertex adjacency, inverse iteration -> 256;
+c4 512 face boxes with sides drawn from [8, 96], 16 parts each in one batched
+call.  Under torchrun each rank runs the same workload on its own GPU
+(independent replicas, no collective on the data path); the value is all
+ranks' elements bisected divided by the slowest rank's time.
 """
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import os
+import platform
+import re
 import statistics
 import subprocess
 import sys
@@ -33,16 +42,54 @@ sys.path.insert(0, ROOT)
 
 METRIC = "elements bisected/s (full RSB to P parts)"
 UNIT = "elements/s"
+
 WORKLOADS = {
-    "c2": {"dims": (64, 64, 32), "adjacency": "face", "parts": 64, "method": "lanczos",
-           "degenerate": "resolve"},
-    "c1": {"dims": (16, 8, 4), "adjacency": "face", "parts": 8, "method": "lanczos",
-           "degenerate": "resolve"},
+    "c1": {"kind": "box", "dims": (16, 8, 4), "adjacency": "face", "parts": 8,
+           "opts": {"method": "lanczos", "degenerate_policy": "resolve"},
+           "name": "box 16x8x4 hex mesh, face-adjacency dual graph, unit weights, 512 elements "
+                   "-> 8 parts (3 levels)"},
+    "c2": {"kind": "box", "dims": (64, 64, 32), "adjacency": "face", "parts": 64,
+           "opts": {"method": "lanczos", "degenerate_policy": "resolve"},
+           "name": "box 64x64x32 hex mesh, face-adjacency dual graph, unit weights, 131072 "
+                   "elements -> 64 parts (6 levels)"},
+    "c3": {"kind": "deleted", "dims": (192, 128, 96), "frac": 0.10, "seed": 20260,
+           "adjacency": "vertex", "parts": 256,
+           "opts": {"method": "inverse", "degenerate_policy": "none", "polish_cycles": 8},
+           "name": "box 192x128x96 hex mesh with a seeded 10% of elements deleted (largest "
+                   "component, 2123367 elements), vertex-adjacency dual graph, weights 4/2/1, "
+                   "inverse iteration with CG -> 256 parts (8 levels)"},
+    "c4": {"kind": "batch", "count": 512, "lo": 8, "hi": 96, "seed": 2026, "adjacency": "face",
+           "parts": 16, "opts": {"method": "lanczos", "degenerate_policy": "resolve"},
+           "name": "batch of 512 box hex meshes with sides drawn from [8, 96], face adjacency, "
+                   "unit weights, 16 parts each (4 levels), one batched call"},
+    "c5": {"kind": "deleted", "dims": (256, 256, 256), "frac": 0.05, "seed": 20261,
+           "adjacency": "vertex", "parts": 1024,
+           "opts": {"method": "lanczos", "degenerate_policy": "none"},
+           "name": "box 256x256x256 hex mesh with a seeded 5% of elements deleted (largest "
+                   "component, 15938356 elements), vertex-adjacency dual graph, weights 4/2/1, "
+                   "mixed-precision Lanczos -> 1024 parts (10 levels)"},
 }
-# bounded sample for the CPU oracle: one level-3 segment of the 64x64x32
-# recursion (a 32x32x16 box) bisected to 8 parts, i.e. levels 3-5 of the same
-# workload
-CPU_SAMPLE = {"dims": (32, 32, 16), "parts": 8}
+DEFAULT_FORMS = {"c1": ["fp64", "fp64_plain", "spmv", "cpu"],
+                 "c2": ["fp64", "fp64_plain", "spmv", "cpu"],
+                 "c3": ["fp64", "spmv", "cpu"], "c4": ["fp64", "cpu"],
+                 "c5": ["fp64", "spmv", "cpu"]}
+# bounded samples for the CPU oracle: meshes of the same kind as the workload
+# (same generator, adjacency, weights and deletion fraction), small enough for
+# a few to a few tens of seconds of host time
+CPU_SAMPLES = {
+    "c5": {"dims": (32, 32, 32), "frac": 0.05, "seed": 20261, "adjacency": "vertex", "parts": 8,
+           "ref_dims": (32, 32, 16), "ref_parts": 2,
+           "opts": {"method": "lanczos", "degenerate": "none"}},
+    "c3": {"dims": (48, 32, 24), "frac": 0.10, "seed": 20260, "adjacency": "vertex", "parts": 8,
+           "ref_dims": (24, 16, 12), "ref_parts": 2,
+           "opts": {"method": "inverse", "degenerate": "none"}},
+    "c2": {"dims": (32, 32, 16), "frac": 0.0, "adjacency": "face", "parts": 8, "ref_parts": 8,
+           "opts": {"method": "lanczos", "degenerate": "resolve"}},
+    "c1": {"dims": (16, 8, 4), "frac": 0.0, "adjacency": "face", "parts": 8, "ref_parts": 8,
+           "opts": {"method": "lanczos", "degenerate": "resolve"}},
+    "c4": {"dims": (24, 20, 16), "frac": 0.0, "adjacency": "face", "parts": 16, "ref_parts": 16,
+           "opts": {"method": "lanczos", "degenerate": "resolve"}},
+}
 
 
 def _peaks():
@@ -60,61 +107,98 @@ def _dist():
     return ws, rank
 
 
+def _cpu_model():
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True).stdout
+        m = re.search(r"Model name:\s*(.+)", out)
+        if m:
+            return m.group(1).strip()
+    except Exception:
+        pass
+    return platform.processor() or platform.machine()
+
+
+def build_graphs(W):
+    """The workload's meshes (meshgen's seeded generators)."""
+    from meshgen import batch_box_dims, box_graph, box_graph_deleted
+
+    if W["kind"] == "box":
+        return [box_graph(*W["dims"], W["adjacency"])]
+    if W["kind"] == "deleted":
+        return [box_graph_deleted(*W["dims"], W["frac"], W["seed"], W["adjacency"])]
+    return [box_graph(*d, W["adjacency"]) for d in batch_box_dims(W["count"], W["lo"], W["hi"],
+                                                                   W["seed"])]
+
+
 # ----------------------------------------------------------------------------
-# CPU oracle (reference arm and cpu_baseline)
+# CPU oracle (reference arm and cpu_baseline), run in a child process with its
+# BLAS threads set to the host's cores
 # ----------------------------------------------------------------------------
 _ORACLE_CHILD = r"""
 import json, sys, time
 sys.path.insert(0, {root!r})
 import oracle as O
-from meshgen import box_graph
-g = box_graph(*{dims!r})
-t = time.perf_counter()
-part = O.rsb_partition(g, {parts})
-dt = time.perf_counter() - t
-ok = bool((part == O.box_partition_closed_form(*{dims!r}, {parts})).all())
-levels = ({parts} - 1).bit_length()
-print(json.dumps({{"seconds": dt, "elements_bisected": g.n * levels, "ok": ok}}))
+from meshgen import box_graph, box_graph_deleted
+S = {sample!r}
+if S["frac"] > 0:
+    g = box_graph_deleted(*S["dims"], S["frac"], S["seed"], S["adjacency"])
+else:
+    g = box_graph(*S["dims"], S["adjacency"])
+P = {parts}
+times = []
+for _ in range({reps}):
+    t = time.perf_counter()
+    part = O.rsb_partition(g, P, O.Options(**S["opts"]))
+    times.append(time.perf_counter() - t)
+levels = (P - 1).bit_length()
+print(json.dumps({{"seconds": times, "elements_bisected": g.n * levels, "n": g.n}}))
 """
 
 
-def run_oracle_sample(dims, parts, threads=1):
+def run_oracle_sample(sample, parts, threads, reps=1):
+    """Times `reps` oracle partitions of the sample in one child process; returns
+    {"seconds": [per rep], "elements_bisected": per rep, "n": elements}."""
     env = dict(os.environ)
     for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
         env[k] = str(threads)
-    code = _ORACLE_CHILD.format(root=ROOT, dims=tuple(dims), parts=parts)
+    code = _ORACLE_CHILD.format(root=ROOT, sample=sample, parts=parts, reps=reps)
     p = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env)
     if p.returncode != 0:
         raise RuntimeError(p.stderr[-2000:])
     return json.loads(p.stdout.strip().splitlines()[-1])
 
 
+def _sample_text(S, parts, n):
+    kind = f"{int(S['frac'] * 100)}%-deleted " if S["frac"] > 0 else ""
+    return (f"FP64 oracle on a {kind}{S['dims'][0]}x{S['dims'][1]}x{S['dims'][2]} "
+            f"{S['adjacency']}-adjacency box of the workload's kind ({n} elements) bisected "
+            f"to {parts} parts, {S['opts']['method']}")
+
+
 def reference_arm(args):
     ws, rank = _dist()
     if rank != 0:
         return 0
-    d, P = CPU_SAMPLE["dims"], CPU_SAMPLE["parts"]
-    for _ in range(args.warmup):
-        run_oracle_sample(d, P)
-    times, units = [], 0
-    ok = True
-    for _ in range(args.steps):
-        r = run_oracle_sample(d, P)
-        times.append(r["seconds"])
-        units += r["elements_bisected"]
-        ok = ok and r["ok"]
+    S = dict(CPU_SAMPLES[args.workload])
+    S["dims"] = S.get("ref_dims", S["dims"])
+    P = S["ref_parts"]
+    threads = os.cpu_count() or 1
+    r = run_oracle_sample(S, P, threads, reps=args.warmup + args.steps)
+    times = r["seconds"][args.warmup:]
+    units = r["elements_bisected"] * args.steps
+    n = r["n"]
     total = sum(times)
     value = units / total
-    sample = (f"oracle on one {d[0]}x{d[1]}x{d[2]} level-3 segment of the 64x64x32 recursion, "
-              f"bisected to {P} parts (levels 3-5; {units // args.steps} elements bisected per step)")
+    sample = _sample_text(S, P, n) + f"; host: {_cpu_model()}, {threads} cores"
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD_NAME, "sample": sample, "matches_closed_form": ok},
+        "warmup": args.warmup, "ms_per_step": 1e3 * statistics.median(times),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOADS[args.workload]["name"], "sample": sample},
         "impl": "reference",
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": sample},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                         "sample": sample, "cpu_model": _cpu_model()},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -155,7 +239,7 @@ class Clocks:
         except Exception:
             self.proc.kill()
         self.f.close()
-        sm, smax, reasons = [], None, set()
+        sm, smax, reasons, power = [], None, set(), []
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for ln in open(self.path):
             p = [x.strip() for x in ln.split(",")]
@@ -164,6 +248,7 @@ class Clocks:
             try:
                 sm.append(float(p[1]))
                 smax = float(p[2])
+                power.append(float(p[3]))
             except ValueError:
                 continue
             for nm, v in zip(names, p[5:9]):
@@ -173,7 +258,7 @@ class Clocks:
         if not sm:
             return None
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": sorted(reasons),
-                "samples": len(sm)}
+                "samples": len(sm), "power_w_median": statistics.median(power) if power else None}
 
 
 # ----------------------------------------------------------------------------
@@ -197,60 +282,102 @@ def aggregate(total_ms: float, units: float, dist=None, device=None):
 
 
 # ----------------------------------------------------------------------------
-# our arm
+# roofline of the dominant kernel family
 # ----------------------------------------------------------------------------
 LAUNCH_NAMES = ["kernels", "cuda_graph", "persistent_cycle", "persistent_resident"]
-KERNEL_NAMES = {
-    ("cycle", 3): ("k_lz_res (one cooperative launch per Fiedler solve: SpMV, CGS2 against the "
-                   "shared-memory-resident basis, Jacobi Ritz pairs, thick restart; FP32 stage "
-                   "and FP64 polish)"),
-    ("cycle", 2): "k_lz_cycle (one cooperative launch per Lanczos cycle)",
+FAMILIES = {
+    "lz_a": "k_lz_a1 (FP32 Lanczos step A: SpMV w = L q_j of the sliced-ELL graph, q_j = w / beta)",
+    "lz_a2": ("k_lz_a2 (FP32 Lanczos step A: first Gram-Schmidt dots of w with the basis, "
+              "staged in shared memory by bulk copies)"),
+    "lz_b": ("k_lz_bt (FP32 Lanczos step B: w -= Q c1 and second Gram-Schmidt dots, basis "
+             "staged by bulk copies)"),
+    "lz_c": "k_lz_c (FP32 Lanczos step C: w -= Q c2 and ||w||)",
+    "cg_ap": "k_cg_ap (CG: Ap = L p and p.Ap)",
+    "cycle": ("k_lz_res (one cooperative launch per Fiedler solve: SpMV, CGS2 against the "
+              "shared-memory-resident basis, Jacobi Ritz pairs, thick restart)"),
 }
-WORKLOAD_NAME = ("box 64x64x32 hex mesh, face-adjacency dual graph, unit weights, "
-                 "131072 elements -> 64 parts (6 levels)")
+PROFILE_KERNEL = {"lz_a": "k_lz_a1", "lz_a2": "k_lz_a2", "lz_b": "k_lz_bt", "lz_c": "k_lz_c",
+                  "cg_ap": "k_cg_ap", "cycle": "k_lz_res"}
 
 
+def _source_sha():
+    h = hashlib.sha256()
+    for f in ("solver.cu", "rsb_internal.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_2606_14659_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def traffic_ratio(kernel, workload):
+    """DRAM bytes / algorithmic bytes of `kernel` from a committed ncu summary
+    (profiles/<kernel>_*_<workload>*.md with lines 'dram_over_algorithmic = x'
+    and 'solver_sha = s'); None when absent or when the kernel sources changed
+    since the capture."""
+    pdir = os.path.join(ROOT, "profiles")
+    try:
+        files = sorted(os.listdir(pdir))
+    except OSError:
+        return None
+    for fn in files:
+        if not (fn.startswith(kernel + "_") and workload in fn and fn.endswith(".md")):
+            continue
+        txt = open(os.path.join(pdir, fn)).read()
+        m = re.search(r"dram_over_algorithmic\s*=\s*([0-9.eE+-]+)", txt)
+        s = re.search(r"solver_sha\s*=\s*([0-9a-f]+)", txt)
+        if m and s and s.group(1) == _source_sha():
+            return float(m.group(1))
+    return None
+
+
+# ----------------------------------------------------------------------------
+# our arm
+# ----------------------------------------------------------------------------
 def our_arm(args):
     import numpy as np
     import torch
 
     import paper_2606_14659_gb300 as R
-    from meshgen import box_graph
 
     ws, rank = _dist()
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
+    dev = f"cuda:{local}"
     dist = None
     if ws > 1:
         import torch.distributed as dist
 
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     W = WORKLOADS[args.workload]
-    g = box_graph(*W["dims"], W["adjacency"])
+    forms = args.forms if args.forms is not None else DEFAULT_FORMS[args.workload]
+    t_gen = time.perf_counter()
+    gs = build_graphs(W)
+    gen_s = time.perf_counter() - t_gen
     P = W["parts"]
-    G = R.graph(g, device=f"cuda:{local}")
-    opts = R.options(method=W["method"], precision=args.precision, degenerate_policy=W["degenerate"],
-                     batched=1, use_graph=args.launch if args.launch is not None else 3)
-    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=f"cuda:{local}")
-    out = torch.empty(g.n, dtype=torch.int32, device=f"cuda:{local}")
+    Gs = [R.graph(g, device=dev) for g in gs]
+    n_total = sum(g.n for g in gs)
+    opts = R.options(precision=args.precision, batched=1,
+                     use_graph=args.launch if args.launch is not None else 3, **W["opts"])
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    outs = [torch.empty(g.n, dtype=torch.int32, device=dev) for g in gs]
     tuned = None
     if args.launch is None:  # autotuned tile rows and launch mode (before the timed region)
-        opts, tune_ms = R.rsb_autotune([G], [P], opts, outs=[out])
+        opts, tune_ms = R.rsb_autotune(Gs, [P] * len(Gs), opts, outs=outs)
         tuned = {"tile_rows": opts.tile_rows, "launch": LAUNCH_NAMES[opts.use_graph],
                  "candidates_ms": {f"{t}x{LAUNCH_NAMES[l]}": round(v, 3)
                                    for (t, l), v in tune_ms.items()}}
 
-    def step():
-        return R.rsb_partition(G, P, opts, out=out, allow_noconv=True)
+    def step(o=opts, graphs=Gs, out=outs):
+        if len(graphs) == 1:
+            p, st, code = R.rsb_partition(graphs[0], P, o, out=out[0], allow_noconv=True)
+            return [p], st, code
+        return R.rsb_partition_batch(graphs, [P] * len(graphs), o, outs=out, allow_noconv=True)
 
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
     # timed region: device-resident inputs, L2 flushed between steps
-    fam = args.profile if args.profile != "auto" else ("cycle" if opts.use_graph in (2, 3)
-                                                        else "lz_b")
     clocks = Clocks(local)
-    ms_steps, units, launches = [], 0, 0
+    ms_steps, units, launches, codes = [], 0, 0, set()
+    resid_max = 0.0
     if dist is not None:
         dist.barrier()
     torch.cuda.synchronize()
@@ -266,117 +393,172 @@ def our_arm(args):
         ms_steps.append(e0.elapsed_time(e1))
         units += st["elements_bisected"]
         launches += st["kernel_launches"]
+        codes.add(code)
+        resid_max = max(resid_max, st["resid_max"])
+        lam_first = st["lambda_first"]
     torch.cuda.synchronize()
     clk = clocks.stop()
     if dist is not None:
         dist.barrier()
-    # the same steps again with the dominant kernel family bracketed by CUDA
-    # events (kept out of the headline timing: the event records add time)
-    prof_ms_steps = []
-    R.rsb_profile_begin(fam)
-    for _ in range(args.steps):
-        flush.zero_()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record()
-        step()
-        e1.record()
-        e1.synchronize()
-        prof_ms_steps.append(e0.elapsed_time(e1))
-    prof_ms, prof_launches, prof_bytes = R.rsb_profile_end()
-    total_ms, units_all = aggregate(sum(ms_steps), units, dist, f"cuda:{local}")
+    units_per_step = units / max(1, args.steps)
+    med = statistics.median(ms_steps)
+    total_ms, units_all = aggregate(med * args.steps, units, dist, dev)
     value = units_all / (total_ms / 1e3)
+
+    # one more step with every kernel family bracketed by CUDA events on the
+    # library's stream (kept out of the headline timing: the records add time)
+    R.rsb_profile_begin("all")
+    flush.zero_()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    step()
+    e1.record()
+    e1.synchronize()
+    prof_step_ms = e0.elapsed_time(e1)
+    R.rsb_profile_end()
+    fam = {}
+    for name in FAMILIES:
+        ms, nl, by = R.rsb_profile_read(name)
+        if nl:
+            fam[name] = {"ms": round(ms, 3), "launches": nl, "gbs": by / (ms * 1e6) if ms else 0.0,
+                         "share": ms / prof_step_ms}
+    dom = max(fam, key=lambda k: fam[k]["ms"]) if fam else None
+
     # correctness of what was timed (outside the timed region)
-    from oracle import box_partition_closed_form  # noqa: WPS433  (check only)
+    check = {}
+    if W["kind"] in ("box", "batch"):
+        from oracle import NotClean, box_partition_closed_form  # noqa: WPS433  (check only)
 
-    ok = bool(np.array_equal(out.cpu().numpy(), box_partition_closed_form(*W["dims"], P)))
+        clean, equal = 0, 0
+        dims_list = [W["dims"]] if W["kind"] == "box" else [
+            g.dims for g in gs]
+        for d, o in zip(dims_list, outs):
+            try:
+                cf = box_partition_closed_form(*d, P)
+            except NotClean:
+                continue
+            clean += 1
+            equal += int(np.array_equal(o.cpu().numpy(), cf))
+        check = {"closed_form_meshes": clean, "closed_form_equal": equal}
+    else:
+        sizes = np.bincount(outs[0].cpu().numpy(), minlength=P)
+        n = gs[0].n
+        expect = [(p + 1) * n // P - p * n // P for p in range(P)]
+        check = {"sizes_exact": bool(np.array_equal(sizes, expect)),
+                 "lambda_first": lam_first, "resid_max_over_dmax": resid_max}
+    check["status_codes"] = sorted(codes)
 
-    # end to end through the public API with pinned host buffers
-    Gh = R.Graph(g.n, torch.from_numpy(np.ascontiguousarray(g.row_ptr)).pin_memory(),
-                 torch.from_numpy(np.ascontiguousarray(g.col, dtype=np.int32)).pin_memory(),
-                 torch.from_numpy(np.ascontiguousarray(g.w, dtype=np.int32)).pin_memory(),
-                 torch.from_numpy(np.ascontiguousarray(g.gid)).pin_memory(), "host")
-    out_h = torch.empty(g.n, dtype=torch.int32).pin_memory()
-    h2d = 8 * (g.n + 1) + 4 * g.nnz + 4 * g.nnz + 8 * g.n
-    d2h = 4 * g.n
-    R.rsb_partition(Gh, P, opts, out=out_h)
-    e2e_ms = []
-    e2e_units = 0
-    for _ in range(max(1, args.steps)):
+    # end to end through the public API: pinned host CSR in, host part ids out
+    Gh, outs_h, h2d, d2h = [], [], 0, 0
+    for g in gs:
+        rp = torch.from_numpy(np.ascontiguousarray(g.row_ptr, dtype=np.int64)).pin_memory()
+        col = torch.from_numpy(np.ascontiguousarray(g.col, dtype=np.int32)).pin_memory()
+        w = torch.from_numpy(np.ascontiguousarray(g.w, dtype=np.int32)).pin_memory()
+        gid = torch.from_numpy(np.ascontiguousarray(g.gid, dtype=np.int64)).pin_memory()
+        Gh.append(R.Graph(g.n, rp, col, w, gid, "host"))
+        outs_h.append(torch.empty(g.n, dtype=torch.int32).pin_memory())
+        h2d += rp.numel() * 8 + col.numel() * 4 + w.numel() * 4 + gid.numel() * 8
+        d2h += g.n * 4
+    e2e_steps = max(1, min(args.steps, args.e2e_steps))
+    e2e_ms, e2e_units = [], 0
+    for _ in range(e2e_steps):
         flush.zero_()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        _, st, _ = R.rsb_partition(Gh, P, opts, out=out_h)
+        _, st, _ = step(graphs=Gh, out=outs_h)
         torch.cuda.synchronize()
         e2e_ms.append(1e3 * (time.perf_counter() - t0))
         e2e_units += st["elements_bisected"]
     e2e_val = e2e_units / (sum(e2e_ms) / 1e3) * (ws if ws > 1 else 1)
+    del Gh, outs_h
 
     extra = {}
-    if rank == 0 and not args.quick:
+    if rank == 0:
         # FP64 forms of the same workload (the mixed batched form must beat them)
         for name, kw in (("fp64_batched", dict(precision="fp64", batched=1)),
                          ("fp64_plain", dict(precision="fp64", batched=0))):
-            o2 = R.options(method=W["method"], degenerate_policy=W["degenerate"],
-                           use_graph=opts.use_graph, tile_rows=opts.tile_rows, **kw)
-            R.rsb_partition(G, P, o2, out=out)
+            form = "fp64" if name == "fp64_batched" else "fp64_plain"
+            if form not in forms or args.precision == "fp64" and name == "fp64_batched":
+                continue
+            o2 = R.options(use_graph=opts.use_graph, tile_rows=opts.tile_rows,
+                           **{**W["opts"], **{k: v for k, v in kw.items()}})
             torch.cuda.synchronize()
+            flush.zero_()
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
-            flush.zero_()
             e0.record()
-            _, st2, _ = R.rsb_partition(G, P, o2, out=out)
+            _, st2, code2 = step(o=o2)
             e1.record()
             e1.synchronize()
-            extra[name] = st2["elements_bisected"] / (e0.elapsed_time(e1) / 1e3)
-        # Laplacian action bandwidth on a graph larger than L2
-        gs = box_graph(192, 128, 96, "vertex")
-        Gs = R.graph(gs, device=f"cuda:{local}")
-        sp = {}
-        for f32 in (True, False):
-            ms, by = R.rsb_laplacian_bench(Gs, f32, 20)
-            sp["f32_gbs" if f32 else "f64_gbs"] = by / (ms * 1e6)
-        sp["graph"] = "192x128x96 vertex adjacency, 4/2/1 weights, %d nnz" % gs.nnz
-        extra["spmv"] = sp
-        del Gs
+            ms2 = e0.elapsed_time(e1)
+            v2 = st2["elements_bisected"] / (ms2 / 1e3)
+            extra[name] = {"value": v2, "ms": round(ms2, 1), "status": code2, "steps": 1,
+                           "mixed_speedup": (value / max(ws, 1)) / v2 if v2 else None}
+        if "spmv" in forms:
+            # Laplacian action bandwidth on the workload's level-0 graph (larger than L2)
+            sp = {}
+            for f32 in (True, False):
+                ms, by = R.rsb_laplacian_bench(Gs[0], f32, 20)
+                sp["f32_gbs" if f32 else "f64_gbs"] = by / (ms * 1e6)
+            sp["graph"] = f"level-0 graph of the workload ({gs[0].n} rows, {gs[0].nnz} nnz)"
+            peak, _ = _peaks()
+            sp["f32_frac"] = sp["f32_gbs"] / peak
+            extra["spmv"] = sp
 
     peak, peak_kind = _peaks()
-    achieved = (prof_bytes / (prof_ms * 1e6)) if prof_ms > 0 else 0.0
+    roof = None
+    if dom is not None:
+        ms, nl, by = R.rsb_profile_read(dom)
+        achieved = by / (ms * 1e6) if ms > 0 else 0.0
+        ratio = traffic_ratio(PROFILE_KERNEL[dom], args.workload)
+        roof = {"bound": "hbm", "kernel": FAMILIES[dom], "achieved": achieved, "peak": peak,
+                "unit": "GB/s", "frac": achieved / peak if peak else None,
+                "traffic": (ratio * by / nl) if ratio is not None and nl else None,
+                "algorithmic_bytes_per_launch": by / nl if nl else None,
+                "peak_kind": peak_kind, "launches_timed": nl,
+                "avg_launch_us": 1e3 * ms / nl if nl else None,
+                "share_of_step": fam[dom]["share"],
+                "timed_in": "one extra profiled step of the same workload and options, every "
+                            "kernel family bracketed by CUDA events on the library's stream",
+                "families": fam}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "warmup": args.warmup, "ms_per_step": med,
+        "ms_per_step_mean": statistics.fmean(ms_steps), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
         "dtype": "f32/f64" if args.precision == "mixed" else "f64",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD_NAME, "method": W["method"], "precision": args.precision,
+        "config": {"workload": W["name"], "key": args.workload, "precision": args.precision,
+                   "options": {k: v for k, v in W["opts"].items()},
                    "batched": True, "launch": LAUNCH_NAMES[opts.use_graph],
-                   "tile_rows": opts.tile_rows, "autotune": tuned, "elements": g.n, "parts": P,
-                   "l2": "flushed between steps (256 MiB write)", "matches_closed_form": ok},
+                   "tile_rows": opts.tile_rows, "autotune": tuned, "elements": n_total,
+                   "meshes": len(gs), "parts": P,
+                   "elements_bisected_per_step": units_per_step,
+                   "l2": "flushed between steps (256 MiB write); inputs larger than L2"
+                         if n_total > 4_000_000 else "flushed between steps (256 MiB write)",
+                   "value_from": "median step time", "input_build_s": round(gen_s, 1),
+                   "check": check},
         "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d,
-                "d2h_bytes_per_step": d2h},
+                "d2h_bytes_per_step": d2h, "steps": e2e_steps},
         "gpu_launches": launches,
-        "roofline": {"bound": "hbm",
-                     "kernel": KERNEL_NAMES.get((fam, opts.use_graph),
-                                                f"lanczos kernel family '{fam}'"),
-                     "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak if peak else None, "traffic": None,
-                     "peak_kind": peak_kind, "launches_timed": prof_launches,
-                     "avg_launch_us": 1e3 * prof_ms / prof_launches if prof_launches else None,
-                     "share_of_step": prof_ms / sum(prof_ms_steps) if prof_ms_steps else None,
-                     "timed_in": "profiled repeat of the timed steps (same workload and options)"},
+        "roofline": roof,
         "clocks": clk,
     }
     line.update(extra)
-    if rank == 0 and not args.quick:
+    if rank == 0 and "cpu" in forms and not args.quick:
         try:
-            d, Pc = CPU_SAMPLE["dims"], CPU_SAMPLE["parts"]
-            r = run_oracle_sample(d, Pc)
+            S = CPU_SAMPLES[args.workload]
+            threads = os.cpu_count() or 1
+            r = run_oracle_sample(S, S["parts"], threads)
+            sec = r["seconds"][0]
             line["cpu_baseline"] = {
-                "value": r["elements_bisected"] / r["seconds"], "unit": UNIT, "cores": 1,
-                "kind": "oracle",
-                "sample": (f"oracle on one {d[0]}x{d[1]}x{d[2]} level-3 segment of the 64x64x32 "
-                           f"recursion bisected to {Pc} parts ({r['elements_bisected']} "
-                           f"elements bisected, {r['seconds']:.1f} s)")}
+                "value": r["elements_bisected"] / sec, "unit": UNIT, "cores": threads,
+                "kind": "oracle", "cpu_model": _cpu_model(),
+                "sample": (_sample_text(S, S["parts"], r["n"]) +
+                           f"; {r['elements_bisected']} elements bisected in "
+                           f"{sec:.1f} s; numpy BLAS on {threads} threads (the sparse "
+                           f"product runs on one)")}
         except Exception as e:  # pragma: no cover
             line["cpu_baseline"] = {"error": str(e)[-300:]}
     if rank == 0:
@@ -386,22 +568,71 @@ def our_arm(args):
     return 0
 
 
+# ----------------------------------------------------------------------------
+# small fixed cases for ncu captures
+# ----------------------------------------------------------------------------
+def case_main(args):
+    import torch
+
+    import paper_2606_14659_gb300 as R
+    from meshgen import box_graph, box_graph_deleted
+
+    if args.frac > 0:
+        g = box_graph_deleted(*args.dims, args.frac, args.seed, args.adjacency)
+    else:
+        g = box_graph(*args.dims, args.adjacency)
+    G = R.graph(g)
+    if args.case == "lanczos":
+        o = R.options(precision=args.precision, max_restarts=args.cycles, tol=1e-14,
+                      mixed_tol=1e-14, use_graph=args.launch if args.launch is not None else 1,
+                      polish_cycles=0)
+        lam, v, res, code = R.rsb_fiedler(G, o)
+        torch.cuda.synchronize()
+        print(f"lanczos {args.dims} {args.adjacency} {args.precision}: {args.cycles} cycles, "
+              f"lambda {lam:.6e}, resid {res:.2e}")
+    elif args.case == "spmv":
+        f32 = args.precision == "mixed"
+        ms, by = R.rsb_laplacian_bench(G, f32, args.reps)
+        print(f"spmv {args.dims} {args.adjacency} {'f32' if f32 else 'f64'}: {ms:.4f} ms, "
+              f"{by / ms / 1e6:.0f} GB/s")
+    else:
+        part, st, code = R.rsb_partition(G, args.parts, R.options(
+            precision=args.precision, use_graph=args.launch if args.launch is not None else 3))
+        torch.cuda.synchronize()
+        print(f"partition {args.dims} -> {args.parts}: {st['levels']} levels, "
+              f"{st['kernel_launches']} launches, code {code}")
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="c2", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="c5", choices=sorted(WORKLOADS))
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
-    ap.add_argument("--profile", default="auto",
-                    choices=["auto", "cycle", "lz_a", "lz_b", "lz_c", "cg_ap"])
+    ap.add_argument("--forms", nargs="*", default=None,
+                    help="extras beside the headline: fp64 (FP64 batched), fp64_plain (FP64, one "
+                         "segment at a time), spmv (Laplacian bandwidth), cpu (oracle baseline)")
+    ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--launch", type=int, default=None, choices=[0, 1, 2, 3],
                     help="fix the Lanczos launch mode (0 kernels, 1 CUDA graph per cycle, "
                          "2 persistent kernel per cycle, 3 resident persistent kernel per "
                          "solve) instead of autotuning it with the tile rows")
-    ap.add_argument("--quick", action="store_true", help="skip the FP64/SpMV/CPU extras")
+    ap.add_argument("--quick", action="store_true", help="skip the CPU baseline")
+    ap.add_argument("--case", choices=["lanczos", "spmv", "partition"], default=None,
+                    help="run one small fixed case (for ncu) instead of the benchmark")
+    ap.add_argument("--dims", type=int, nargs=3, default=[192, 128, 96])
+    ap.add_argument("--adjacency", default="face", choices=["face", "vertex"])
+    ap.add_argument("--frac", type=float, default=0.0)
+    ap.add_argument("--seed", type=int, default=20261)
+    ap.add_argument("--cycles", type=int, default=2)
+    ap.add_argument("--parts", type=int, default=64)
+    ap.add_argument("--reps", type=int, default=5)
     args = ap.parse_args()
+    if args.case:
+        return case_main(args)
     if args.impl == "reference":
         return reference_arm(args)
     return our_arm(args)

@@ -16,17 +16,25 @@ extern "C" {
 /*
  * Kernel timing for bandwidth accounting (not part of the method).
  * rsb_profile_begin(family) makes the following calls bracket every launch of
- * one kernel family with CUDA events on the library's stream and add up the
- * algorithmic bytes of each launch; rsb_profile_end() returns the totals and
- * switches timing off.  family: 1 Lanczos step A (SpMV + first Gram-Schmidt
- * dots), 2 step B (update + second dots), 3 step C (update + norm), 4 CG
- * Laplacian action, 5 Laplacian action of rsb_laplacian_bench, 6 the
- * persistent Lanczos-cycle kernel (bytes of its A, B and C phases).
+ * one kernel family (or of every family, RSB_PROF_ALL) with CUDA events on the
+ * library's stream and add up the algorithmic bytes of each launch;
+ * rsb_profile_end() returns the totals over the timed families and switches
+ * timing off; rsb_profile_read() then gives one family's totals.  Families:
+ *   1 Lanczos step A: the SpMV launch k_lz_a1 (FP32) or the fused k_lz_a (FP64)
+ *   2 step B (update + second Gram-Schmidt dots)
+ *   3 step C (update + norm)
+ *   4 CG Laplacian action (inverse iteration)
+ *   5 Laplacian action of rsb_laplacian_bench
+ *   6 the persistent Lanczos kernels (bytes of all of their phases)
+ *   7 FP32 step A's first Gram-Schmidt dots, k_lz_a2
  * Bytes count 4 B per stored SELL entry (padding included), every vector
- * element read or written once, and FP64 deflation vectors.
+ * element read or written once, and FP64 deflation vectors.  The event
+ * records add a few microseconds per launch, so profiled calls run slower.
  */
+#define RSB_PROF_ALL (-1)
 void rsb_profile_begin(int family);
 void rsb_profile_end(double *ms_total, int64_t *launches, double *bytes_total);
+void rsb_profile_read(int family, double *ms, int64_t *launches, double *bytes);
 
 /*
  * Failure-path test hook (not part of the method).  While on != 0, the

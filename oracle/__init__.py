@@ -12,7 +12,7 @@ Lanczos / inverse-iteration agreement and the spectral cut bound.
 from .rsb_oracle import (  # noqa: F401
     Options, FiedlerResult, rows_of, degree, laplacian_apply, laplacian_dense, induced,
     components, jacobi_eigh, splitmix64, start_vector, adjacency_csr,
-    lanczos_fiedler, inverse_fiedler, cg_solve, fiedler, orient, split_k,
+    lanczos_fiedler, block_lanczos_fiedler, inverse_fiedler, cg_solve, fiedler, orient, split_k,
     weighted_cut, quartic_rotate, fiedler_candidates, split_connected, bisect,
     seg_size, rsb_partition, fiedler_of_graph, partition_metrics,
 )

@@ -103,6 +103,7 @@ class Options:
     cluster_tol: float = 0.05
     tie_rel: float = 1e-5
     breakdown: float = 1e-14
+    block: int = 1                   # Lanczos block width (1: single-vector Lanczos)
 
 
 @dataclass
@@ -396,7 +397,122 @@ def inverse_fiedler(g, opts: Options, deflate=(), start=None):
     return FiedlerResult(lam, y, res, opts.max_outer, False, inner)
 
 
+def _block_start(gid, seed, nd, b, cycle=0):
+    """Start block: column c is the start vector of seed + (c + b * cycle) * 2^32
+    (column 0 of the first cycle is the single-vector start)."""
+    return np.stack([start_vector(gid, (seed + ((c + b * cycle) << 32)) % (1 << 64), nd)
+                     for c in range(b)], axis=1)
+
+
+def _chol_scaled(G: np.ndarray, tiny: float, pivot_min: float):
+    """Upper R with G = R^T R, from the Cholesky factor of the correlation matrix
+    D^-1 G D^-1 (D = sqrt diag G); None when a column is tiny (norm <= tiny) or
+    the columns are nearly dependent (a scaled pivot^2 below pivot_min)."""
+    d = np.sqrt(np.maximum(np.diag(G), 0.0))
+    if (d <= tiny).any():
+        return None
+    Gs = G / np.outer(d, d)
+    try:
+        Rs = np.linalg.cholesky(Gs).T
+    except np.linalg.LinAlgError:
+        return None
+    if (np.diag(Rs) ** 2 < pivot_min).any():
+        return None
+    return Rs * d[None, :]
+
+
+def block_lanczos_fiedler(g, opts: Options, deflate=(), start=None):
+    """Fiedler pair by thick-restarted block Lanczos of width b = opts.block.
+
+    The single-vector method of §6 (reading R3) with a block of b vectors per
+    step, the extension §9 names for nearly repeated lambda_2: each block step
+    normalises the residual block W by a Cholesky QR (Q_new = W R^-1, G = W^T W
+    = R^T R, factored on the correlation matrix), applies L to it, and
+    re-orthogonalises Z = L Q_new by two classical Gram-Schmidt passes against
+    [1/sqrt(n), deflation vectors, q_0 .. q_{j+b-1}]; the passes' coefficients
+    on the basis are the b new columns of S = Q^T L Q.  A cycle adds blocks
+    while the basis has room for one (m = krylov_dim columns), then takes the
+    Ritz pairs of S, y = Q s_1 and its residual; the thick restart keeps the
+    kk smallest Ritz vectors, kk = keep + ((m - keep) mod b) so that whole
+    blocks fill the basis, and continues from the residual block.  A block whose
+    columns are (nearly) dependent ends the cycle early; the next cycle then
+    restarts from y and fresh start columns.  Graphs with fewer than
+    krylov_dim + b dimensions orthogonal to the fixed basis use the
+    single-vector method.
+    """
+    n = g.n
+    nd = len(deflate)
+    dim = n - 1 - nd
+    if dim <= 0:
+        return None
+    b = max(1, int(opts.block))
+    m = min(opts.krylov_dim, dim)
+    if b == 1 or dim < opts.krylov_dim + b:
+        return lanczos_fiedler(g, opts, deflate, start)
+    B = _fixed_basis(n, deflate)
+    nb = B.shape[1]
+    dmax = float(degree(g).max())
+    tiny = opts.breakdown * dmax
+    W = _block_start(g.gid, opts.seed, nd, b)
+    if start is not None:
+        W[:, 0] = np.asarray(start, dtype=np.float64)
+    W, _ = _cgs(B, W)
+    W, _ = _cgs(B, W)
+    BV = np.zeros((n, nb + m))
+    BV[:, :nb] = B
+    V = BV[:, nb:]
+    S = np.zeros((m, m))
+    kk_restart = opts.keep + (m - opts.keep) % b
+    j0 = 0
+    theta, y, res = 0.0, None, np.inf
+    for cycle in range(1, opts.max_restarts + 1):
+        j, broke = j0, False
+        while j + b <= m:
+            R = _chol_scaled(W.T @ W, tiny, 1e-12)
+            if R is None:
+                broke = True
+                break
+            V[:, j:j + b] = W @ np.linalg.inv(R)
+            Z = np.stack([laplacian_apply(g, V[:, j + c]) for c in range(b)], axis=1)
+            basis = BV[:, :nb + j + b]
+            Z, C1 = _cgs(basis, Z)
+            Z, C2 = _cgs(basis, Z)
+            col = (C1 + C2)[nb:, :]                  # (j + b) x b
+            S[:j, j:j + b] = col[:j]
+            S[j:j + b, :j] = col[:j].T
+            S[j:j + b, j:j + b] = 0.5 * (col[j:] + col[j:].T)
+            W = Z
+            j += b
+        meff = j
+        if meff == 0:
+            break
+        thetas, Y = np.linalg.eigh(S[:meff, :meff])
+        theta = float(thetas[0])
+        y = V[:, :meff] @ Y[:, 0]
+        y = y / np.linalg.norm(y)
+        res = float(np.linalg.norm(laplacian_apply(g, y) - theta * y))
+        if res <= opts.tol * dmax:
+            return FiedlerResult(theta, y, res, cycle, True)
+        S[:] = 0.0
+        kk = min(kk_restart, meff - 1)
+        if broke or kk <= 0:
+            W = _block_start(g.gid, opts.seed, nd, b, cycle)
+            W[:, 0] = y
+            W, _ = _cgs(B, W)
+            W, _ = _cgs(B, W)
+            j0 = 0
+            continue
+        V[:, :kk] = V[:, :meff] @ Y[:, :kk]
+        S[np.arange(kk), np.arange(kk)] = thetas[:kk]
+        j0 = kk
+    if y is None:
+        return lanczos_fiedler(g, opts, deflate, start)
+    return FiedlerResult(theta, y, res, opts.max_restarts, False)
+
+
 def fiedler(g, opts: Options, deflate=(), start=None):
+    if opts.method == "lanczos" and opts.block > 1:
+        return block_lanczos_fiedler(g, opts, deflate, start)
     if opts.method == "lanczos":
         return lanczos_fiedler(g, opts, deflate, start)
     if opts.method == "inverse":

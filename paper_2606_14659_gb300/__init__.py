@@ -7,5 +7,5 @@ from . import rsb  # noqa: F401
 from .rsb import (  # noqa: F401
     Graph, graph, options, rsb_partition, rsb_partition_batch, rsb_fiedler,
     rsb_laplacian_apply, rsb_laplacian_bench, rsb_release, RSBError, rsb_profile_begin,
-    rsb_profile_end, rsb_autotune,
+    rsb_profile_end, rsb_profile_read, rsb_autotune,
 )

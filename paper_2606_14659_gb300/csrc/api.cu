@@ -113,18 +113,24 @@ static void trace_mark(cudaStream_t s, const char* fmt, ...) {
 // kernel timing (rsb_profile_begin / rsb_profile_end)
 // ----------------------------------------------------------------------------
 static struct {
-  int family = PROF_NONE;
+  unsigned mask = 0;  // enabled families (bit f for family f)
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pool;
+  std::vector<int> pool_family;
   std::vector<int> free_list, pending;
   bool capturing = false;
   std::vector<int> captured;
-  double ms = 0.0;
-  long long launches = 0;
-  unsigned long long* dbytes = nullptr;  // one counter per family
+  double ms[PROF_NFAM] = {0};
+  long long launches[PROF_NFAM] = {0};
+  double bytes[PROF_NFAM] = {0};
+  unsigned long long* dbytes = nullptr;  // one device counter per family
 } g_prof;
 
+static bool prof_on(int family) {
+  return family > PROF_NONE && family < PROF_NFAM && (g_prof.mask >> family & 1u);
+}
+
 int prof_before(int family, cudaStream_t s) {
-  if (g_prof.family == PROF_NONE || family != g_prof.family) return -1;
+  if (!prof_on(family)) return -1;
   int idx;
   if (!g_prof.free_list.empty()) {
     idx = g_prof.free_list.back();
@@ -133,8 +139,10 @@ int prof_before(int family, cudaStream_t s) {
     cudaEvent_t a, b;
     if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) return -1;
     g_prof.pool.emplace_back(a, b);
+    g_prof.pool_family.push_back(0);
     idx = (int)g_prof.pool.size() - 1;
   }
+  g_prof.pool_family[idx] = family;
   cudaEventRecordWithFlags(g_prof.pool[idx].first, s,
                            g_prof.capturing ? cudaEventRecordExternal : cudaEventRecordDefault);
   return idx;
@@ -150,8 +158,9 @@ void prof_collect() {
   for (int idx : g_prof.pending) {
     float t = 0.f;
     if (cudaEventElapsedTime(&t, g_prof.pool[idx].first, g_prof.pool[idx].second) == cudaSuccess) {
-      g_prof.ms += t;
-      g_prof.launches += 1;
+      const int f = g_prof.pool_family[idx];
+      g_prof.ms[f] += t;
+      g_prof.launches[f] += 1;
     } else {
       cudaGetLastError();
     }
@@ -171,37 +180,56 @@ std::vector<int> prof_capture_end() {
 void prof_replay(const std::vector<int>& pairs) {
   g_prof.pending.insert(g_prof.pending.end(), pairs.begin(), pairs.end());
 }
-int prof_family() { return g_prof.family; }
 
 unsigned long long* prof_bytes(int family) {
-  if (g_prof.family == PROF_NONE || family != g_prof.family || !g_prof.dbytes) return nullptr;
-  return g_prof.dbytes;
+  if (!prof_on(family) || !g_prof.dbytes) return nullptr;
+  return g_prof.dbytes + family;
 }
 
 extern "C" void rsb_profile_begin(int family) {
-  g_prof.family = (family >= PROF_LZ_A && family <= PROF_CYCLE) ? family : PROF_NONE;
-  g_prof.ms = 0.0;
-  g_prof.launches = 0;
+  if (family == RSB_PROF_ALL) g_prof.mask = ((1u << PROF_NFAM) - 1u) & ~1u;
+  else g_prof.mask = (family > PROF_NONE && family < PROF_NFAM) ? (1u << family) : 0u;
+  for (int f = 0; f < PROF_NFAM; ++f) {
+    g_prof.ms[f] = 0.0;
+    g_prof.launches[f] = 0;
+    g_prof.bytes[f] = 0.0;
+  }
   g_prof.pending.clear();
   // pairs held by graphs that were destroyed are free again
   g_prof.free_list.clear();
   for (int i = 0; i < (int)g_prof.pool.size(); ++i) g_prof.free_list.push_back(i);
-  if (!g_prof.dbytes && cudaMalloc(&g_prof.dbytes, sizeof(unsigned long long)) != cudaSuccess) {
+  const size_t nb = sizeof(unsigned long long) * PROF_NFAM;
+  if (!g_prof.dbytes && cudaMalloc(&g_prof.dbytes, nb) != cudaSuccess) {
     cudaGetLastError();
     g_prof.dbytes = nullptr;
   }
-  if (g_prof.dbytes) cudaMemset(g_prof.dbytes, 0, sizeof(unsigned long long));
+  if (g_prof.dbytes) cudaMemset(g_prof.dbytes, 0, nb);
 }
 
 extern "C" void rsb_profile_end(double* ms_total, int64_t* launches, double* bytes_total) {
   cudaDeviceSynchronize();
   prof_collect();
-  unsigned long long b = 0;
-  if (g_prof.dbytes) cudaMemcpy(&b, g_prof.dbytes, sizeof(b), cudaMemcpyDeviceToHost);
-  if (ms_total) *ms_total = g_prof.ms;
-  if (launches) *launches = g_prof.launches;
-  if (bytes_total) *bytes_total = (double)b;
-  g_prof.family = PROF_NONE;
+  unsigned long long b[PROF_NFAM] = {0};
+  if (g_prof.dbytes) cudaMemcpy(b, g_prof.dbytes, sizeof(b), cudaMemcpyDeviceToHost);
+  double ms = 0.0, by = 0.0;
+  long long nl = 0;
+  for (int f = 0; f < PROF_NFAM; ++f) {
+    g_prof.bytes[f] = (double)b[f];
+    ms += g_prof.ms[f];
+    nl += g_prof.launches[f];
+    by += g_prof.bytes[f];
+  }
+  if (ms_total) *ms_total = ms;
+  if (launches) *launches = nl;
+  if (bytes_total) *bytes_total = by;
+  g_prof.mask = 0;
+}
+
+extern "C" void rsb_profile_read(int family, double* ms, int64_t* launches, double* bytes) {
+  const bool ok = family > PROF_NONE && family < PROF_NFAM;
+  if (ms) *ms = ok ? g_prof.ms[family] : 0.0;
+  if (launches) *launches = ok ? g_prof.launches[family] : 0;
+  if (bytes) *bytes = ok ? g_prof.bytes[family] : 0.0;
 }
 
 int devbuf_reserve(DevBuf& b, size_t bytes) {

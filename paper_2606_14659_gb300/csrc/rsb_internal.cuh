@@ -415,9 +415,8 @@ void rsb_count_launch(int k = 1);
 // Kernel timing (rsb_profile_begin/end): families of include/rsb.h.
 enum {
   PROF_NONE = 0, PROF_LZ_A = 1, PROF_LZ_B = 2, PROF_LZ_C = 3, PROF_CG_AP = 4, PROF_SPMV = 5,
-  PROF_CYCLE = 6
+  PROF_CYCLE = 6, PROF_LZ_A2 = 7, PROF_NFAM = 8
 };
-int prof_family();
 int prof_before(int family, cudaStream_t s);      // event pair index or -1
 void prof_after(int idx, cudaStream_t s);
 void prof_collect();                              // after a stream sync

@@ -56,6 +56,7 @@ struct LzArgs {
   int* n_active;
   long long* stat_cycles;
   unsigned long long* pb_a;  // profiling byte counters (nullptr when off)
+  unsigned long long* pb_a2;
   unsigned long long* pb_b;
   unsigned long long* pb_c;
   unsigned long long* pb_cg;
@@ -657,7 +658,7 @@ __global__ void __launch_bounds__(RSB_BLOCK, 2) k_lz_a2(LzArgs<V> a, int j, Grid
     const V* Qc = Qb + (size_t)(ci & 1) * slots * CRB + (c0 - (c0 & ~(AL - 1)));
     const V* ws = Qc + (size_t)nq * CRB;
     const int nr = c1 - c0;
-    if (a.pb_a && (int)threadIdx.x < nr)
+    if (a.pb_a2 && (int)threadIdx.x < nr)
       pbytes += sizeof(V) * (unsigned long long)(1 + j) + 8ull * nd;
 #pragma unroll
     for (int i = 0; i < MAXCW; ++i) {
@@ -677,7 +678,7 @@ __global__ void __launch_bounds__(RSB_BLOCK, 2) k_lz_a2(LzArgs<V> a, int j, Grid
     __syncthreads();
   }
   store_dots<V>(a, nc, acc, blockIdx.x);
-  if (a.pb_a) prof_add(a.pb_a, pbytes);
+  if (a.pb_a2) prof_add(a.pb_a2, pbytes);
   if (last_cta(&u.cnt, u.ntile)) {
     final_reduce(a.partials, a.stride, u.tile0, u.ntile, nc, out);
     if (threadIdx.x == 0) {
@@ -1513,9 +1514,9 @@ static LzArgs<V> make_args(const LevelGraph& G, const Tile* tiles, int ntiles, U
   a.n_active = B.n_active;
   a.stat_cycles = B.stat_cycles;
   a.pb_a = prof_bytes(PROF_LZ_A);
+  a.pb_a2 = prof_bytes(PROF_LZ_A2);
   a.pb_b = prof_bytes(PROF_LZ_B);
   a.pb_c = prof_bytes(PROF_LZ_C);
-  if (prof_family() == PROF_CYCLE) a.pb_a = a.pb_b = a.pb_c = prof_bytes(PROF_CYCLE);
   a.pb_cg = prof_bytes(PROF_CG_AP);
   a.S = B.S;
   a.jmin = B.jmin;
@@ -1565,6 +1566,8 @@ static int lz_cycle(LzArgs<V>& a, int ntiles, int nunits, int M, double breakdow
     if (sizeof(V) == 4) {
       k_lz_a1<V><<<ntiles, RSB_BLOCK, 0, s>>>(a, j);
       RSB_CKL("k_lz_a1");
+      prof_after(pi, s);
+      pi = prof_before(PROF_LZ_A2, s);
       k_lz_a2<V><<<ntiles, RSB_BLOCK, lz_bt_smem<V>(j + 2), s>>>(a, j, gb);
       RSB_CKL("k_lz_a2");
     } else {
@@ -1637,7 +1640,9 @@ static int lanczos_run(const LevelGraph& G, const Tile* tiles, int ntiles, Unit*
         int maxcyc = B.maxcycles + 1;
         double bd = breakdown;
         GridBar* gb = B.gb;
-        void* args[] = {(void*)&a, (void*)&M, (void*)&trs, (void*)&bd, (void*)&nunits,
+        LzArgs<V> ar = a;  // the persistent kernel's phases count into one family
+        ar.pb_a = ar.pb_a2 = ar.pb_b = ar.pb_c = prof_bytes(PROF_CYCLE);
+        void* args[] = {(void*)&ar, (void*)&M, (void*)&trs, (void*)&bd, (void*)&nunits,
                         (void*)&maxcyc, (void*)&gb};
         const int pi = prof_before(PROF_CYCLE, s);
         cudaError_t e = cudaLaunchCooperativeKernel((const void*)k_lz_res<V>, ntiles, RSB_BLOCK,
@@ -1658,9 +1663,11 @@ static int lanczos_run(const LevelGraph& G, const Tile* tiles, int ntiles, Unit*
     const int grid = std::max(1, std::min(ntiles, occ * nsm));
     GridBar* gb = B.gb;
     int jstart = 0;
+    LzArgs<V> ar = a;  // the persistent kernel's phases count into one family
+    ar.pb_a = ar.pb_a2 = ar.pb_b = ar.pb_c = prof_bytes(PROF_CYCLE);
     for (int cyc = 0; cyc < 100000; ++cyc) {
       RSB_CK(cudaMemsetAsync(B.jmin, 0x7F, sizeof(int), s));
-      void* args[] = {(void*)&a, (void*)&jstart, (void*)&M, (void*)&breakdown, (void*)&ntiles,
+      void* args[] = {(void*)&ar, (void*)&jstart, (void*)&M, (void*)&breakdown, (void*)&ntiles,
                       (void*)&nunits, (void*)&gb};
       const int pi = prof_before(PROF_CYCLE, s);
       cudaError_t e = cudaLaunchCooperativeKernel((const void*)k_lz_cycle<V>, grid, RSB_BLOCK,

@@ -25,7 +25,7 @@ EXPORTED = ["rsb_options_default", "rsb_partition", "rsb_partition_batch", "rsb_
             "rsb_laplacian_apply", "rsb_laplacian_apply_f32", "rsb_laplacian_bench",
             "rsb_strerror", "rsb_last_error_detail", "rsb_release", "rsb_profile_begin",
             "rsb_profile_end", "rsb_laplacian_apply_noalloc", "rsb_autotune",
-            "rsb_test_poison_barrier"]
+            "rsb_test_poison_barrier", "rsb_profile_read"]
 
 RSB_TUNE_CANDIDATES = 6
 TUNE_CANDIDATES = [(2, 3), (4, 3), (8, 3), (2, 1), (4, 1), (8, 1)]  # (tile_rows, use_graph)
@@ -98,6 +98,9 @@ def load():
     lib.rsb_profile_end.argtypes = [C.POINTER(C.c_double), C.POINTER(C.c_int64),
                                     C.POINTER(C.c_double)]
     lib.rsb_profile_end.restype = None
+    lib.rsb_profile_read.argtypes = [C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_int64),
+                                     C.POINTER(C.c_double)]
+    lib.rsb_profile_read.restype = None
     for name in ("rsb_partition", "rsb_partition_batch", "rsb_fiedler", "rsb_autotune",
                  "rsb_laplacian_apply",
                  "rsb_laplacian_apply_f32", "rsb_laplacian_bench", "rsb_laplacian_apply_noalloc"):
@@ -335,7 +338,8 @@ def rsb_release():
     load().rsb_release()
 
 
-PROFILE_FAMILIES = {"lz_a": 1, "lz_b": 2, "lz_c": 3, "cg_ap": 4, "spmv": 5, "cycle": 6}
+PROFILE_FAMILIES = {"lz_a": 1, "lz_b": 2, "lz_c": 3, "cg_ap": 4, "spmv": 5, "cycle": 6,
+                    "lz_a2": 7, "all": -1}
 
 
 def rsb_profile_begin(family: str | int):
@@ -345,9 +349,19 @@ def rsb_profile_begin(family: str | int):
 
 
 def rsb_profile_end():
-    """(total ms, launches, algorithmic bytes) of the profiled family."""
+    """(total ms, launches, algorithmic bytes) of the profiled families."""
     ms = C.c_double(0.0)
     n = C.c_int64(0)
     by = C.c_double(0.0)
     load().rsb_profile_end(C.byref(ms), C.byref(n), C.byref(by))
+    return ms.value, n.value, by.value
+
+
+def rsb_profile_read(family: str | int):
+    """(ms, launches, algorithmic bytes) of one family of the last profiled interval."""
+    fam = PROFILE_FAMILIES[family] if isinstance(family, str) else int(family)
+    ms = C.c_double(0.0)
+    n = C.c_int64(0)
+    by = C.c_double(0.0)
+    load().rsb_profile_read(fam, C.byref(ms), C.byref(n), C.byref(by))
     return ms.value, n.value, by.value

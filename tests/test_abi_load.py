@@ -27,7 +27,8 @@ def test_header_declares_the_boundary():
               "rsb_options_default", "rsb_release", "rsb_laplacian_apply"):
         assert n in names
     hooks = _declared(["rsb_test.h"])
-    assert set(hooks) == {"rsb_profile_begin", "rsb_profile_end", "rsb_test_poison_barrier"}
+    assert set(hooks) == {"rsb_profile_begin", "rsb_profile_end", "rsb_profile_read",
+                         "rsb_test_poison_barrier"}
     assert not set(hooks) & set(names)
 
 
