@@ -51,7 +51,7 @@ enum {
   RSB_EDISCONNECTED = 6  /* rsb_fiedler: the graph has several components      */
 };
 
-enum { RSB_LANCZOS = 0, RSB_INVERSE = 1 };          /* §6, §7                    */
+enum { RSB_LANCZOS = 0, RSB_INVERSE = 1, RSB_RCB = 2 }; /* §6, §7; RCB of §5/§8 */
 enum { RSB_FP64 = 0, RSB_MIXED = 1 };               /* arithmetic of the solves  */
 enum { RSB_DEGEN_NONE = 0, RSB_DEGEN_RESOLVE = 1 }; /* repeated lambda_2 (§9)    */
 
@@ -65,6 +65,9 @@ enum { RSB_DEGEN_NONE = 0, RSB_DEGEN_RESOLVE = 1 }; /* repeated lambda_2 (§9)  
  *            are 1, 2, 4 shared vertices); NULL means every weight is 1
  *   gid      int64[n], global element ids used for tie-breaks and start
  *            vectors, distinct within one graph; NULL means gid = row index
+ *   coords   double[3 n], (x, y, z) of every element (e.g. its centroid), row
+ *            by row; needed only by method RSB_RCB and by reorder = 1, else
+ *            may be NULL
  */
 typedef struct rsb_csr {
   int64_t n;
@@ -72,10 +75,16 @@ typedef struct rsb_csr {
   const int32_t *col;
   const int32_t *weight;
   const int64_t *gid;
+  const double *coords;
 } rsb_csr;
 
 typedef struct rsb_options {
-  int method;            /* RSB_LANCZOS | RSB_INVERSE                              */
+  int method;            /* RSB_LANCZOS | RSB_INVERSE: the Fiedler vector (§6, §7);
+                            RSB_RCB: recursive coordinate bisection instead (the
+                            geometric partitioner §5 and §8 run before RSB): every
+                            segment splits along the axis of its largest coordinate
+                            extent, lower coordinates left, ties by gid; needs
+                            coords                                                  */
   int precision;         /* RSB_FP64 | RSB_MIXED (FP32 vectors + FP64 polish)      */
   int krylov_dim;        /* Lanczos steps per cycle, 2..40                         */
   int max_restarts;      /* Lanczos cycles per solve (paper §8: 50)                */
@@ -104,6 +113,17 @@ typedef struct rsb_options {
   int tile_rows;         /* rows per thread of a solver tile (a tile is 256 x this
                             many rows of one subgraph), 1..64; 0: the default 2     */
   int polish_dim;        /* MIXED: Lanczos steps per FP64 polish cycle, 2..40      */
+  int block;             /* Lanczos block width, 1..4: 1 the single-vector method of
+                            §6; 2..4 thick-restarted block Lanczos (the block
+                            extension of §9) for every subgraph with at least
+                            krylov_dim + block dimensions orthogonal to the fixed
+                            basis, single-vector for smaller ones                  */
+  int reorder;           /* 1: before the spectral recursion, order every mesh's
+                            elements by recursive coordinate bisection into leaves
+                            of 512..1023 elements (the RCB pre-partition of §5/§8;
+                            on one GPU it makes the Laplacian's gathers local);
+                            part ids are still returned in caller order; needs
+                            coords.  0: keep the caller's order                    */
 } rsb_options;
 
 typedef struct rsb_stats {
@@ -122,7 +142,8 @@ typedef struct rsb_stats {
 /* Fills *o with the defaults: Lanczos, FP64, krylov_dim 40, max_restarts 50,
  * tol 1e-10, cg_tol 1e-12, cg_maxit 4000, max_outer 50, RESOLVE,
  * cluster_tol 0.05, tie_rel 1e-5, mixed_tol 1e-6, batched 1, use_graph 3,
- * validate 0, polish_cycles 2, keep 8, tile_rows 0, polish_dim 16. */
+ * validate 0, polish_cycles 2, keep 8, tile_rows 0, polish_dim 16, block 1,
+ * reorder 0. */
 void rsb_options_default(rsb_options *o);
 
 /*
@@ -205,6 +226,53 @@ int rsb_laplacian_apply_f32(const rsb_csr *g, const float *x, float *y, void *st
  */
 int rsb_laplacian_bench(const rsb_csr *g, int f32, int reps, double *ms_per_apply,
                         double *useful_bytes, void *stream);
+
+/*
+ * The element dual graph of a mesh given as element -> global vertex ids
+ * (§2: elements are adjacent when they share a vertex, the weight omega is the
+ * number of shared vertices; §5: the same graph is P^T Q Q^T P without its
+ * diagonal).  Built on the GPU: the elements at every vertex are collected
+ * (a counting sort by vertex id), then every element's distinct neighbours
+ * are counted and written in ascending order.
+ *   ne       number of elements, 1 <= ne < 2^29
+ *   nv       vertices per element, 1..8 (8 for hexes)
+ *   ev       int64[ne * nv], the vertex ids of element e at ev[e*nv .. e*nv+nv-1],
+ *            each in [0, 2^31)
+ *   row_ptr  int64[ne + 1] out (device or host)
+ *   col, weight  int32[cap] out, or both NULL to learn nnz first
+ *   cap      room in col and weight
+ *   nnz      host int64 out: the number of stored entries
+ * Rows list columns in ascending order with weights 1..7 (the CSR rsb_partition
+ * takes).  RSB_EINVAL for ids outside [0, 2^31), an element meeting more than
+ * 256 others at its vertices, two elements sharing more than 7 vertices, or
+ * cap < nnz (row_ptr and nnz are still written then).
+ */
+int rsb_dual_graph(int64_t ne, int nv, const int64_t *ev, int64_t *row_ptr, int32_t *col,
+                   int32_t *weight, int64_t cap, int64_t *nnz, void *stream);
+
+/*
+ * y = L x without a stored graph: the gather-scatter form of §5,
+ * L = D_w - A_w with A_w = P^T Q Q^T P.  Every element's value is summed per
+ * global vertex (Q^T P x), and element e collects sum over its vertices v of
+ * (c_v x_e - w_v), c_v the number of elements at v and w_v their sum: the
+ * weighted Laplacian of the dual graph above.  ne, nv, ev as in
+ * rsb_dual_graph; x, y double[ne] (or float[ne] for the _f32 form), device or
+ * host.  The vertex buckets are rebuilt by every call.
+ */
+int rsb_laplacian_apply_gs(int64_t ne, int nv, const int64_t *ev, const double *x, double *y,
+                           void *stream);
+int rsb_laplacian_apply_gs_f32(int64_t ne, int nv, const int64_t *ev, const float *x, float *y,
+                               void *stream);
+
+/*
+ * Times `reps` gather-scatter Laplacian applications (two kernels each; FP64
+ * when f32 == 0) after building the vertex buckets once; *ms_per_apply gets
+ * the mean device time of one application, *useful_bytes its algorithmic
+ * bytes (bucket offsets twice, the bucket entries and vertex ids once each,
+ * x read once, the vertex sums written and read once, y written once).
+ */
+int rsb_laplacian_bench_gs(int64_t ne, int nv, const int64_t *ev, int f32, int reps,
+                           double *ms_per_apply, double *useful_bytes, void *stream);
 
 /*
  * rsb_laplacian_apply_noalloc — y = L x (FP64) like rsb_laplacian_apply, for

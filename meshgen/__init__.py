@@ -15,4 +15,5 @@ from .boxes import (  # noqa: F401
     random_graph,
     disjoint_union,
     quad_vertex_lists_dual,
+    permute_graph,
 )

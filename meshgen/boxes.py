@@ -59,6 +59,37 @@ class DualGraph:
         """Row index of every stored entry (int64[nnz])."""
         return np.repeat(np.arange(self.n, dtype=np.int64), np.diff(self.row_ptr))
 
+    def box_index(self) -> np.ndarray:
+        """Box element index i + nx (j + ny k) of every row (box meshes only)."""
+        if "box_index" in self.meta:
+            return self.meta["box_index"]
+        if self.meta.get("kind") == "box_deleted":
+            return self.meta["orig_gid"]
+        if self.meta.get("kind") == "box":
+            return self.gid
+        raise ValueError("not a box mesh")
+
+    def centroids(self) -> np.ndarray:
+        """Element centroids (n x 3, float64): element (i, j, k) of a box with unit
+        spacing has its centre at (i + 1/2, j + 1/2, k + 1/2)."""
+        nx, ny, _ = self.dims
+        idx = self.box_index()
+        return np.stack([idx % nx, (idx // nx) % ny, idx // (nx * ny)], axis=1) + 0.5
+
+    def hex_vertices(self) -> np.ndarray:
+        """Global vertex ids of every element's 8 corners (n x 8, int64): corner
+        (a, b, c) in {0,1}^3 of element (i, j, k) is mesh vertex
+        (i + a) + (nx + 1) ((j + b) + (ny + 1) (k + c)), listed with a fastest."""
+        nx, ny, _ = self.dims
+        idx = self.box_index()
+        i, j, k = idx % nx, (idx // nx) % ny, idx // (nx * ny)
+        out = np.empty((len(idx), 8), dtype=np.int64)
+        for c in range(2):
+            for b in range(2):
+                for a in range(2):
+                    out[:, a + 2 * b + 4 * c] = (i + a) + (nx + 1) * ((j + b) + (ny + 1) * (k + c))
+        return out
+
 
 def _offsets(adjacency: str):
     if adjacency == "face":
@@ -264,3 +295,30 @@ def quad_vertex_lists_dual(vertex_lists: list[list[int]]) -> DualGraph:
             if s:
                 edges[(a, b)] = s
     return _graph_from_edges(m, edges, np.arange(m, dtype=np.int64), {"kind": "vertex_lists"})
+
+
+def permute_graph(g: DualGraph, seed: int) -> DualGraph:
+    """The same graph with its rows in a seeded random order (numpy PCG64);
+    every element keeps its gid (and its box position), so any method that
+    depends only on gids and the graph gives the same answer."""
+    rng = np.random.default_rng(seed)
+    perm = rng.permutation(g.n)          # new row r holds old row perm[r]
+    inv = np.empty(g.n, dtype=np.int64)
+    inv[perm] = np.arange(g.n)
+    lens = np.diff(g.row_ptr)[perm]
+    row_ptr = np.zeros(g.n + 1, dtype=np.int64)
+    np.cumsum(lens, out=row_ptr[1:])
+    starts = g.row_ptr[perm]
+    take = np.repeat(starts - row_ptr[:-1], lens) + np.arange(row_ptr[-1])
+    col = inv[g.col[take]].astype(np.int32)
+    w = g.w[take]
+    meta = dict(g.meta)
+    try:
+        meta["box_index"] = g.box_index()[perm]
+    except ValueError:
+        pass
+    meta["perm"] = perm
+    # columns of each row ascending again
+    rows = np.repeat(np.arange(g.n, dtype=np.int64), lens)
+    order = np.lexsort((col, rows))
+    return DualGraph(g.n, row_ptr, col[order], w[order], g.gid[perm].copy(), g.dims, meta)

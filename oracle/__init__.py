@@ -14,7 +14,13 @@ from .rsb_oracle import (  # noqa: F401
     components, jacobi_eigh, splitmix64, start_vector, adjacency_csr,
     lanczos_fiedler, block_lanczos_fiedler, inverse_fiedler, cg_solve, fiedler, orient, split_k,
     weighted_cut, quartic_rotate, fiedler_candidates, split_connected, bisect,
-    seg_size, rsb_partition, fiedler_of_graph, partition_metrics,
+    seg_size, rsb_partition, fiedler_of_graph, partition_metrics, rcb_partition,
+)
+from .amg import (  # noqa: F401
+    laplacian_csr, amg_hierarchy, vcycle, fcg_solve, amg_inverse_fiedler,
+)
+from .gather_scatter import (  # noqa: F401
+    gs_operators, gs_adjacency_apply, gs_laplacian_apply, dual_graph_from_vertices,
 )
 from .box_closed_form import (  # noqa: F401
     NotClean, box_lambda2, box_spectrum, box_fiedler_x, box_partition_closed_form,

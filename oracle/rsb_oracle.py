@@ -104,6 +104,7 @@ class Options:
     tie_rel: float = 1e-5
     breakdown: float = 1e-14
     block: int = 1                   # Lanczos block width (1: single-vector Lanczos)
+    amg: bool = False                # inverse iteration: AMG-preconditioned flexible CG (§7)
 
 
 @dataclass
@@ -515,6 +516,10 @@ def fiedler(g, opts: Options, deflate=(), start=None):
         return block_lanczos_fiedler(g, opts, deflate, start)
     if opts.method == "lanczos":
         return lanczos_fiedler(g, opts, deflate, start)
+    if opts.method == "inverse" and opts.amg:
+        from .amg import amg_inverse_fiedler
+
+        return amg_inverse_fiedler(g, opts, deflate, start)
     if opts.method == "inverse":
         return inverse_fiedler(g, opts, deflate, start)
     raise ValueError(opts.method)
@@ -678,6 +683,32 @@ def rsb_partition(g, P: int, opts: Options | None = None, record=None) -> np.nda
         mem[idx] = True
         sub = induced(g, mem)
         left = bisect(sub, k, opts, record)
+        stack.append((idx[~left], pm, p1))
+        stack.append((idx[left], p0, pm))
+    return part
+
+
+def rcb_partition(coords: np.ndarray, gid: np.ndarray, P: int, tie_rel: float = 1e-5) -> np.ndarray:
+    """Recursive coordinate bisection into P parts (the geometric pre-partitioner
+    §5 and §8 run before RSB): a segment is split along the axis of its largest
+    coordinate extent (the lowest axis on equal extents) at the proportional
+    count of R6, lower coordinates left, equal coordinates (within tie_rel of the
+    extent) left in ascending gid (R7)."""
+    coords = np.asarray(coords, dtype=np.float64)
+    N = len(coords)
+    part = np.full(N, -1, dtype=np.int32)
+    stack = [(np.arange(N, dtype=np.int64), 0, P)]
+    while stack:
+        idx, p0, p1 = stack.pop()
+        if p1 - p0 == 1:
+            part[idx] = p0
+            continue
+        pm = p0 + (p1 - p0) // 2
+        k = (pm * N) // P - (p0 * N) // P
+        c = coords[idx]
+        ext = c.max(axis=0) - c.min(axis=0)
+        axis = int(np.argmax(ext))
+        left = split_k(c[:, axis], gid[idx], k, tie_rel)
         stack.append((idx[~left], pm, p1))
         stack.append((idx[left], p0, pm))
     return part

@@ -30,7 +30,7 @@
 // defined in select.cu / solver.cu / graph.cu (not all in the shared header)
 int launch_orient(const LevelGraph& G, const Tile* tiles, int ntiles, Unit* units,
                   const uint64_t* ckey, const double* v, int cand, double tie_rel,
-                  double* partials, cudaStream_t s);
+                  double* partials, cudaStream_t s, int fixed_sign = 0);
 int launch_select(const LevelGraph& G, const Tile* tiles, int ntiles, Unit* units, int nunits,
                   const uint64_t* ckey, const double* v, int mode, int cand, int* hist,
                   cudaStream_t s);
@@ -49,7 +49,12 @@ int launch_cut(const LevelGraph& G, const Tile* tiles, int ntiles, Unit* units,
 int launch_cc_spread(const LevelGraph& G, const int32_t* parent, const uint64_t* cmin,
                      uint64_t* ckey, int* flag, cudaStream_t s);
 int solver_setup(Unit* units, int nunits, int nd, int krylov, int maxcycles, double tol,
-                 int require_cluster, int keep, SolveBufs& B, cudaStream_t s);
+                 int require_cluster, int keep, SolveBufs& B, cudaStream_t s,
+                 long long dim_lo = 0, long long dim_hi = (1ll << 62));
+int solver_block_lanczos(const LevelGraph& G, const Tile* tiles, int ntiles, Unit* units,
+                         int nunits, const uint64_t* ckey, SolveBufs& SB, int f32, int M, int bw,
+                         int keep, uint64_t seedbase, int use_graph, cudaStream_t s);
+size_t blk_unit_bytes();
 int solver_lanczos(const LevelGraph& G, const Tile* tiles, int ntiles, Unit* units, int nunits,
                    const uint64_t* ckey, SolveBufs& B, int f32, int M, uint64_t sd,
                    const double* from64, const float* from32, int use_graph, cudaStream_t s);
@@ -254,6 +259,7 @@ int devbuf_reserve(DevBuf& b, size_t bytes) {
 // ----------------------------------------------------------------------------
 struct PrecBufs {
   DevBuf Q, W0, W1, Y, X, R, P, AP;
+  DevBuf Z0, Z1;  // block Lanczos: interleaved residual blocks
 };
 
 struct Ctx {
@@ -265,11 +271,15 @@ struct Ctx {
   DevBuf len, slice_sz, scan_tmp, tmp64, newpos;
   DevBuf parent, cmin, ckey, side;
   DevBuf units, tiles, sunits, stiles;
-  DevBuf hist, partials, mom, sbuf;
+  DevBuf hist, partials, mom, sbuf, blk;
   DevBuf cand[3];
   PrecBufs pb[2];  // 0: FP64, 1: FP32
   DevBuf seg_row0, seg_nleft, seg_child0, seg_p0, seg_split, seg_keystar, seg_unit, seg_ncomp;
   DevBuf counters;  // one Counters record
+  DevBuf coords_cat;            // RCB: (x, y, z) per element, caller order, meshes concatenated
+  DevBuf perm, iperm, rcb_home;  // RCB reordering: new row -> caller row and back
+  // gather-scatter (element -> vertex ids): buckets of elements per vertex
+  DevBuf gs_count, gs_cursor, gs_bptr, gs_bucket, gs_ev32, gs_len, gs_rowptr, gs_w, gs_misc;
   DevBuf part_concat;
   int trmax = 0;    // largest tile of the level being solved, rows
   std::vector<DevBuf> stage;  // staged host inputs
@@ -372,16 +382,21 @@ extern "C" void rsb_options_default(rsb_options* o) {
   o->keep = 8;
   o->tile_rows = 0;
   o->polish_dim = 16;
+  o->block = 1;
+  o->reorder = 0;
 }
 
 static int check_options(const rsb_options& o) {
-  if (o.method != RSB_LANCZOS && o.method != RSB_INVERSE) return rsb_set_error(RSB_EINVAL, "method");
+  if (o.method != RSB_LANCZOS && o.method != RSB_INVERSE && o.method != RSB_RCB)
+    return rsb_set_error(RSB_EINVAL, "method");
+  if (o.reorder != 0 && o.reorder != 1) return rsb_set_error(RSB_EINVAL, "reorder");
   if (o.precision != RSB_FP64 && o.precision != RSB_MIXED)
     return rsb_set_error(RSB_EINVAL, "precision");
   if (o.krylov_dim < 1 || o.krylov_dim > RSB_MAXM) return rsb_set_error(RSB_EINVAL, "krylov_dim");
   if (o.keep < 0 || o.keep > RSB_MAXKEEP) return rsb_set_error(RSB_EINVAL, "keep");
   if (o.tile_rows < 0 || o.tile_rows > 64) return rsb_set_error(RSB_EINVAL, "tile_rows");
   if (o.polish_dim < 2 || o.polish_dim > RSB_MAXM) return rsb_set_error(RSB_EINVAL, "polish_dim");
+  if (o.block < 1 || o.block > 4) return rsb_set_error(RSB_EINVAL, "block");
   if (o.use_graph < 0 || o.use_graph > 3) return rsb_set_error(RSB_EINVAL, "use_graph");
   if (o.max_restarts < 1) return rsb_set_error(RSB_EINVAL, "max_restarts");
   if (!(o.tol > 0) || !(o.cg_tol > 0) || !(o.mixed_tol > 0))
@@ -403,10 +418,15 @@ struct MeshIn {
   const int32_t* col;
   const int32_t* wt;
   const int64_t* gid;
+  const double* coords;
   int64_t nnz;
 };
 
-static int build_level0(Ctx& c, const std::vector<MeshIn>& meshes, int validate, LevelGraph& G) {
+// perm / iperm (optional, meshes concatenated, indices local to each mesh): row
+// i of mesh m in the level-0 graph is the caller's row perm[off_m + i], and the
+// caller's row j becomes row iperm[off_m + j]
+static int build_level0(Ctx& c, const std::vector<MeshIn>& meshes, int validate, LevelGraph& G,
+                        const int64_t* perm = nullptr, const int32_t* iperm = nullptr) {
   int64_t N = 0;
   for (auto& m : meshes) N += m.n;
   if (N >= RSB_MAXN) return rsb_set_error(RSB_EINVAL, "too many rows (limit 2^29)");
@@ -422,7 +442,9 @@ static int build_level0(Ctx& c, const std::vector<MeshIn>& meshes, int validate,
   int64_t off = 0;
   for (auto& m : meshes) {
     if ((rc = launch_validate(m.row_ptr, m.col, m.wt, m.n, validate, flag, c.s))) return rc;
-    if ((rc = launch_row_lengths(m.row_ptr, m.n, dptr<int32_t>(c.len) + off, c.s))) return rc;
+    if ((rc = launch_row_lengths(m.row_ptr, m.n, dptr<int32_t>(c.len) + off, c.s,
+                                 perm ? perm + off : nullptr)))
+      return rc;
     off += m.n;
   }
   RSB_CK(cudaMemcpyAsync(c.h_pinned, flag, sizeof(int), cudaMemcpyDeviceToHost, c.s));
@@ -467,7 +489,8 @@ static int build_level0(Ctx& c, const std::vector<MeshIn>& meshes, int validate,
   for (size_t i = 0; i < meshes.size(); ++i) {
     const MeshIn& m = meshes[i];
     if ((rc = launch_fill_sell(m.row_ptr, m.col, m.wt, m.gid, m.n, off, off, (int32_t)i,
-                               G.slice_ptr, G.ent, G.deg, G.gid, G.home, G.row_seg, c.s)))
+                               G.slice_ptr, G.ent, G.deg, G.gid, G.home, G.row_seg, c.s,
+                               perm ? perm + off : nullptr, iperm ? iperm + off : nullptr)))
       return rc;
     off += m.n;
   }
@@ -592,10 +615,37 @@ static int solve_candidate(Ctx& c, const LevelGraph& G, const Tile* tiles, int n
   // stage 1: working precision
   if ((rc = reserve_prec(c, mixed, G.n, std::max(M, 1), B))) return rc;
   const double tol1 = mixed ? std::max(o.tol, o.mixed_tol) : o.tol;
-  if ((rc = solver_setup(units, nunits, nd, o.krylov_dim, o.max_restarts, tol1, require_cluster,
-                         o.keep, B, c.s)))
-    return rc;
   RSB_CK(cudaMemsetAsync(&cn->cycles, 0, sizeof(long long), c.s));
+  // block Lanczos for the units with room for a full basis and one more block;
+  // the single-vector method below takes the rest
+  long long single_hi = 1ll << 62;
+  if (!inverse && o.block > 1) {
+    const long long lo = (long long)o.krylov_dim + o.block;
+    single_hi = lo - 1;
+    if (dim >= lo) {
+      PrecBufs& pb = c.pb[mixed ? 1 : 0];
+      const size_t es = mixed ? sizeof(float) : sizeof(double);
+      if ((rc = devbuf_reserve(pb.Z0, es * 4 * (size_t)(G.n + 32))) ||
+          (rc = devbuf_reserve(pb.Z1, es * 4 * (size_t)(G.n + 32))) ||
+          (rc = devbuf_reserve(c.blk, blk_unit_bytes() * (size_t)nunits)))
+        return rc;
+      B.Z0 = pb.Z0.p;
+      B.Z1 = pb.Z1.p;
+      B.bu = c.blk.p;
+      if ((rc = solver_setup(units, nunits, nd, o.krylov_dim, o.max_restarts, tol1,
+                             require_cluster, o.keep, B, c.s, lo, 1ll << 62)))
+        return rc;
+      if ((rc = solver_block_lanczos(G, tiles, ntiles, units, nunits, ckey, B, mixed,
+                                     o.krylov_dim, o.block, o.keep, o.seed + (uint64_t)nd,
+                                     use_graph, c.s)))
+        return rc;
+      trace_mark(c.s, "cand %d stage 1 (block lanczos %d, %s): %d units, %d tiles", cand,
+                 o.block, mixed ? "fp32" : "fp64", nunits, ntiles);
+    }
+  }
+  if ((rc = solver_setup(units, nunits, nd, o.krylov_dim, o.max_restarts, tol1, require_cluster,
+                         o.keep, B, c.s, 0, single_hi)))
+    return rc;
   if (inverse) {
     const double cgt = mixed ? std::max(o.cg_tol, 1e-6) : o.cg_tol;
     rc = solver_inverse(G, tiles, ntiles, units, nunits, ckey, B, mixed, sd, nullptr, nullptr, cgt,
@@ -670,7 +720,7 @@ static int split_units(Ctx& c, const LevelGraph& G, std::vector<Unit>& hunits,
   int rc;
   if ((rc = devbuf_reserve(c.units, sizeof(Unit) * nunits))) return rc;
   if ((rc = devbuf_reserve(c.tiles, sizeof(Tile) * ntiles))) return rc;
-  if ((rc = devbuf_reserve(c.partials, 2 * sizeof(double) * (size_t)RSB_MAXC * ntiles + 64))) return rc;
+  if ((rc = devbuf_reserve(c.partials, 4 * sizeof(double) * (size_t)RSB_MAXC * ntiles + 64))) return rc;
   if ((rc = devbuf_reserve(c.hist, sizeof(int) * 256 * (size_t)nunits))) return rc;
   if ((rc = devbuf_reserve(c.mom, sizeof(double) * 24 * (size_t)nunits))) return rc;
   if ((rc = devbuf_reserve(c.sbuf, sizeof(double) * RSB_SSTRIDE * (size_t)nunits))) return rc;
@@ -686,6 +736,22 @@ static int split_units(Ctx& c, const LevelGraph& G, std::vector<Unit>& hunits,
   double* partials = dptr<double>(c.partials);
   int64_t maxn = 0;
   for (auto& u : hunits) maxn = std::max<int64_t>(maxn, u.n);
+  if (o.method == RSB_RCB) {
+    // recursive coordinate bisection: the unit's coordinate along its longest
+    // extent takes the place of the Fiedler vector; lower coordinates go left
+    double* v0 = dptr<double>(c.cand[0]);
+    uint8_t* side = dptr<uint8_t>(c.side);
+    int* hist = dptr<int>(c.hist);
+    if ((rc = launch_rcb_vector(G, tiles, ntiles, units, dptr<double>(c.coords_cat), v0, partials,
+                                c.s)) ||
+        (rc = launch_orient(G, tiles, ntiles, units, ckey, v0, 0, o.tie_rel, partials, c.s, 1)) ||
+        (rc = launch_select(G, tiles, ntiles, units, nunits, ckey, v0, 0, 0, hist, c.s)) ||
+        (rc = launch_split_below(G, tiles, ntiles, units, ckey, v0, 0, partials, c.s)) ||
+        (rc = launch_select(G, tiles, ntiles, units, nunits, ckey, v0, 1, 0, hist, c.s)) ||
+        (rc = launch_split_assign(G, tiles, ntiles, units, ckey, v0, side, 0, c.s)))
+      return rc;
+    return RSB_OK;
+  }
   if ((rc = launch_degree_max(G, tiles, ntiles, units, ckey, partials, c.s))) return rc;
   const int ncmax = o.degenerate_policy == RSB_DEGEN_RESOLVE ? 3 : 1;
   for (int cand = 0; cand < ncmax; ++cand) {
@@ -733,12 +799,29 @@ struct MeshInfo {
 
 static inline int64_t fl(int64_t p, int64_t N, int64_t P) { return (p * N) / P; }
 
+// perm / iperm: the level-0 row order (see build_level0); home_out: where to
+// copy the caller row of every row of the final level (the RCB reordering)
 static int run_rsb(Ctx& c, const std::vector<MeshIn>& meshes, const std::vector<int32_t>& nparts,
-                   const rsb_options& o, int32_t* part_concat, rsb_stats* st) {
+                   const rsb_options& o, int32_t* part_concat, rsb_stats* st,
+                   const int64_t* perm = nullptr, const int32_t* iperm = nullptr,
+                   int64_t* home_out = nullptr) {
   LevelGraph G;
   trace_mark(c.s, "call start");
-  int rc = build_level0(c, meshes, o.validate, G);
+  int rc = build_level0(c, meshes, o.validate, G, perm, iperm);
   if (rc) return rc;
+  const bool rcb = o.method == RSB_RCB;
+  if (rcb) {
+    int64_t nall = 0;
+    for (auto& m : meshes) nall += m.n;
+    if ((rc = devbuf_reserve(c.coords_cat, 3 * sizeof(double) * (size_t)(nall + 32)))) return rc;
+    int64_t o3 = 0;
+    for (auto& m : meshes) {
+      if (!m.coords) return rsb_set_error(RSB_EINVAL, "coordinate bisection needs coords");
+      RSB_CK(cudaMemcpyAsync(dptr<double>(c.coords_cat) + o3, m.coords, 3 * sizeof(double) * m.n,
+                             cudaMemcpyDeviceToDevice, c.s));
+      o3 += 3 * m.n;
+    }
+  }
   trace_mark(c.s, "level-0 ingest: %lld rows, %lld stored entries", (long long)G.n,
              (long long)G.nent);
   const int64_t N = G.n;
@@ -800,17 +883,23 @@ static int run_rsb(Ctx& c, const std::vector<MeshIn>& meshes, const std::vector<
     }
     // components of every segment
     if ((rc = devbuf_reserve(c.seg_ncomp, sizeof(int32_t) * nseg))) return rc;
-    RSB_CK(cudaMemsetAsync(c.seg_ncomp.p, 0, sizeof(int32_t) * nseg, c.s));
-    if ((rc = launch_cc(G, dptr<int32_t>(c.parent), dptr<uint64_t>(c.cmin), &cn->flag, c.s))) return rc;
-    if ((rc = launch_cc_spread(G, dptr<int32_t>(c.parent), dptr<uint64_t>(c.cmin),
-                               dptr<uint64_t>(c.ckey), &cn->flag, c.s)))
-      return rc;
-    if ((rc = launch_comp_count(G, dptr<int32_t>(c.parent), dptr<int32_t>(c.seg_ncomp), c.s)))
-      return rc;
-    std::vector<int32_t> ncomp(nseg);
-    RSB_CK(cudaMemcpyAsync(ncomp.data(), c.seg_ncomp.p, sizeof(int32_t) * nseg,
-                           cudaMemcpyDeviceToHost, c.s));
-    RSB_CK(cudaStreamSynchronize(c.s));
+    std::vector<int32_t> ncomp(nseg, 1);
+    if (rcb) {
+      // geometric splits ignore connectivity: every segment is one piece
+      RSB_CK(cudaMemsetAsync(c.ckey.p, 0, sizeof(uint64_t) * (size_t)G.n, c.s));
+    } else {
+      RSB_CK(cudaMemsetAsync(c.seg_ncomp.p, 0, sizeof(int32_t) * nseg, c.s));
+      if ((rc = launch_cc(G, dptr<int32_t>(c.parent), dptr<uint64_t>(c.cmin), &cn->flag, c.s)))
+        return rc;
+      if ((rc = launch_cc_spread(G, dptr<int32_t>(c.parent), dptr<uint64_t>(c.cmin),
+                                 dptr<uint64_t>(c.ckey), &cn->flag, c.s)))
+        return rc;
+      if ((rc = launch_comp_count(G, dptr<int32_t>(c.parent), dptr<int32_t>(c.seg_ncomp), c.s)))
+        return rc;
+      RSB_CK(cudaMemcpyAsync(ncomp.data(), c.seg_ncomp.p, sizeof(int32_t) * nseg,
+                             cudaMemcpyDeviceToHost, c.s));
+      RSB_CK(cudaStreamSynchronize(c.s));
+    }
     // straddling component of segments that fell apart (radix select on the
     // component key with rank nleft)
     std::vector<uint64_t> keystar(nseg, 0);
@@ -890,7 +979,7 @@ static int run_rsb(Ctx& c, const std::vector<MeshIn>& meshes, const std::vector<
     trace_mark(c.s, "level %d components and units", level);
     if ((rc = split_units(c, G, hunits, htiles, o, rs))) return rc;
     trace_mark(c.s, "level %d split (%d units)", level, (int)hunits.size());
-    if (level == 0 && !hunits.empty()) {
+    if (level == 0 && !hunits.empty() && !rcb) {
       Unit u0;
       RSB_CK(cudaMemcpyAsync(&u0, dptr<Unit>(c.units), sizeof(Unit), cudaMemcpyDeviceToHost, c.s));
       RSB_CK(cudaStreamSynchronize(c.s));
@@ -957,6 +1046,9 @@ static int run_rsb(Ctx& c, const std::vector<MeshIn>& meshes, const std::vector<
   RSB_CK(cudaMemcpyAsync(c.seg_child0.p, p0.data(), sizeof(int32_t) * nseg, cudaMemcpyHostToDevice,
                          c.s));
   if ((rc = launch_write_parts(G, dptr<int32_t>(c.seg_child0), part_concat, c.s))) return rc;
+  if (home_out)
+    RSB_CK(cudaMemcpyAsync(home_out, G.home, sizeof(int64_t) * (size_t)G.n,
+                           cudaMemcpyDeviceToDevice, c.s));
   // CC error flag (a bound that can never be reached in a correct run)
   RSB_CK(cudaMemcpyAsync(c.h_pinned, &cn->flag, sizeof(int), cudaMemcpyDeviceToHost, c.s));
   RSB_CK(cudaStreamSynchronize(c.s));
@@ -1020,6 +1112,55 @@ static int mesh_from(Ctx& c, const rsb_csr* g, MeshIn& m) {
   if ((rc = stage_in(c, g->col, (size_t)nnz, &m.col))) return rc;
   if ((rc = stage_in(c, g->weight, (size_t)nnz, &m.wt))) return rc;
   if ((rc = stage_in(c, g->gid, (size_t)g->n, &m.gid))) return rc;
+  if ((rc = stage_in(c, g->coords, (size_t)(3 * g->n), &m.coords))) return rc;
+  return RSB_OK;
+}
+
+__global__ void k_make_perm(const int64_t* __restrict__ home, int64_t n, int64_t off, int64_t* perm,
+                            int32_t* iperm) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int64_t p = home[off + i] - off;
+  perm[off + i] = p;
+  iperm[off + p] = (int32_t)i;
+}
+
+// The RCB order of every mesh: RCB into 2^k leaves of 512..1023 elements; the
+// rows of the final level, in order, are the new row order.
+static int rcb_order(Ctx& c, const std::vector<MeshIn>& meshes, const rsb_options& o,
+                     const int64_t** perm, const int32_t** iperm) {
+  int64_t N = 0;
+  std::vector<int32_t> leaves;
+  for (auto& m : meshes) {
+    if (!m.coords) return rsb_set_error(RSB_EINVAL, "reorder needs coords for every mesh");
+    int32_t p = 1;
+    while ((int64_t)p * 2 * 512 <= m.n) p *= 2;
+    leaves.push_back(p);
+    N += m.n;
+  }
+  int rc;
+  if ((rc = devbuf_reserve(c.perm, sizeof(int64_t) * (size_t)(N + 32))) ||
+      (rc = devbuf_reserve(c.iperm, sizeof(int32_t) * (size_t)(N + 32))) ||
+      (rc = devbuf_reserve(c.rcb_home, sizeof(int64_t) * (size_t)(N + 32))))
+    return rc;
+  rsb_options orcb = o;
+  orcb.method = RSB_RCB;
+  orcb.batched = 1;
+  if ((rc = run_rsb(c, meshes, leaves, orcb, dptr<int32_t>(c.part_concat), nullptr, nullptr,
+                    nullptr, dptr<int64_t>(c.rcb_home))))
+    return rc;
+  int64_t off = 0;
+  for (auto& m : meshes) {
+    if (m.n > 0) {
+      k_make_perm<<<(unsigned)((m.n + RSB_BLOCK - 1) / RSB_BLOCK), RSB_BLOCK, 0, c.s>>>(
+          dptr<int64_t>(c.rcb_home), m.n, off, dptr<int64_t>(c.perm), dptr<int32_t>(c.iperm));
+      RSB_CKL("k_make_perm");
+    }
+    off += m.n;
+  }
+  trace_mark(c.s, "RCB reordering of %lld elements", (long long)N);
+  *perm = dptr<int64_t>(c.perm);
+  *iperm = dptr<int32_t>(c.iperm);
   return RSB_OK;
 }
 
@@ -1053,9 +1194,17 @@ extern "C" int rsb_partition_batch(const rsb_csr* gs, int32_t nmesh, const int32
   }
   if (N >= RSB_MAXN) return end_call(c, stream, rsb_set_error(RSB_EINVAL, "too many rows"));
   rc = devbuf_reserve(c.part_concat, sizeof(int32_t) * (N + 32));
+  const int64_t* perm = nullptr;
+  const int32_t* iperm = nullptr;
+  if (!rc && o.reorder && o.method != RSB_RCB) {
+    // locality reordering: recursive coordinate bisection of every mesh into
+    // leaves of 512 to 1023 elements; the spectral recursion then starts from
+    // the elements in RCB order (the part ids still land in caller order)
+    rc = rcb_order(c, meshes, o, &perm, &iperm);
+  }
   if (!rc) {
     if (o.batched) {
-      rc = run_rsb(c, meshes, np, o, dptr<int32_t>(c.part_concat), st);
+      rc = run_rsb(c, meshes, np, o, dptr<int32_t>(c.part_concat), st, perm, iperm);
     } else {
       // one mesh at a time; statistics summed
       rsb_stats acc;
@@ -1066,7 +1215,8 @@ extern "C" int rsb_partition_batch(const rsb_csr* gs, int32_t nmesh, const int32
         memset(&one, 0, sizeof(one));
         std::vector<MeshIn> single(1, meshes[m]);
         std::vector<int32_t> p1(1, np[m]);
-        const int r1 = run_rsb(c, single, p1, o, dptr<int32_t>(c.part_concat) + off, &one);
+        const int r1 = run_rsb(c, single, p1, o, dptr<int32_t>(c.part_concat) + off, &one,
+                               perm ? perm + off : nullptr, iperm ? iperm + off : nullptr);
         if (r1 && r1 != RSB_ENOCONV) { rc = r1; break; }
         if (r1 == RSB_ENOCONV) rc = RSB_ENOCONV;
         acc.levels = std::max(acc.levels, one.levels);
@@ -1192,6 +1342,7 @@ extern "C" int rsb_fiedler(const rsb_csr* g, const rsb_options* opt, double* lam
   if (opt) o = *opt;
   int rc = check_options(o);
   if (rc) return rc;
+  if (o.method == RSB_RCB) return rsb_set_error(RSB_EINVAL, "rsb_fiedler needs a spectral method");
   Ctx* pc = nullptr;
   rc = begin_call(&pc, stream);
   if (rc) return rc;
@@ -1267,7 +1418,7 @@ extern "C" int rsb_fiedler(const rsb_csr* g, const rsb_options* opt, double* lam
   const int ntiles = (int)htiles.size();
   if ((rc = devbuf_reserve(c.units, sizeof(Unit))) ||
       (rc = devbuf_reserve(c.tiles, sizeof(Tile) * ntiles)) ||
-      (rc = devbuf_reserve(c.partials, 2 * sizeof(double) * (size_t)RSB_MAXC * ntiles + 64)) ||
+      (rc = devbuf_reserve(c.partials, 4 * sizeof(double) * (size_t)RSB_MAXC * ntiles + 64)) ||
       (rc = devbuf_reserve(c.sbuf, sizeof(double) * RSB_SSTRIDE)) ||
       (rc = devbuf_reserve(c.cand[0], sizeof(double) * (N + 32))))
     return end_call(c, stream, rc);
@@ -1395,6 +1546,199 @@ extern "C" int rsb_laplacian_bench(const rsb_csr* g, int f32, int reps, double* 
 
 extern "C" void rsb_test_poison_barrier(int on) { g_rsb_poison_barrier = on ? 1 : 0; }
 
+// ----------------------------------------------------------------------------
+// element -> vertex ids: the dual graph and the matrix-free Laplacian (§5)
+// ----------------------------------------------------------------------------
+int gs_vertex_count(const int64_t* ev, int64_t cnt, unsigned long long* d_vmax, int* d_flag,
+                    int64_t* V, cudaStream_t s);
+int gs_buckets(const int64_t* ev, int64_t ne, int nv, int64_t V, int64_t* count, int64_t* cursor,
+               int64_t* bptr, int32_t* bucket, int32_t* ev32, void* scan_tmp, size_t scan_bytes,
+               cudaStream_t s);
+int gs_row_lengths(int64_t ne, int nv, const int32_t* ev32, const int64_t* bptr,
+                   const int32_t* bucket, int64_t* len, int* d_flag, cudaStream_t s);
+int gs_fill_dual(int64_t ne, int nv, const int32_t* ev32, const int64_t* bptr,
+                 const int32_t* bucket, const int64_t* row_ptr, int32_t* col, int32_t* wt,
+                 cudaStream_t s);
+int gs_apply(int f32, int64_t ne, int nv, int64_t V, const int32_t* ev32, const int64_t* bptr,
+             const int32_t* bucket, const void* x, void* w, void* y, cudaStream_t s);
+
+// Buckets of the elements at every vertex in the context's workspace; *V out.
+static int gs_setup(Ctx& c, int64_t ne, int nv, const int64_t* ev_in, int64_t* V) {
+  if (ne < 1 || ne >= RSB_MAXN || nv < 1 || nv > 8 || !ev_in)
+    return rsb_set_error(RSB_EINVAL, "need 1 <= ne < 2^29, 1 <= nv <= 8 and vertex ids");
+  const int64_t* ev = nullptr;
+  int rc = stage_in(c, ev_in, (size_t)(ne * nv), &ev);
+  if (rc) return rc;
+  if ((rc = devbuf_reserve(c.gs_misc, 256))) return rc;
+  unsigned long long* d_vmax = dptr<unsigned long long>(c.gs_misc);
+  int* d_flag = (int*)(d_vmax + 1);
+  if ((rc = gs_vertex_count(ev, ne * nv, d_vmax, d_flag, V, c.s))) return rc;
+  const int64_t nV = *V;
+  const size_t scan_bytes = scan_tmp_bytes(std::max<int64_t>(nV, ne) + 2);
+  if ((rc = devbuf_reserve(c.gs_count, sizeof(int64_t) * (size_t)(nV + 2))) ||
+      (rc = devbuf_reserve(c.gs_cursor, sizeof(int64_t) * (size_t)(nV + 2))) ||
+      (rc = devbuf_reserve(c.gs_bptr, sizeof(int64_t) * (size_t)(nV + 2))) ||
+      (rc = devbuf_reserve(c.gs_bucket, sizeof(int32_t) * (size_t)(ne * nv))) ||
+      (rc = devbuf_reserve(c.gs_ev32, sizeof(int32_t) * (size_t)(ne * nv))) ||
+      (rc = devbuf_reserve(c.scan_tmp, scan_bytes)))
+    return rc;
+  return gs_buckets(ev, ne, nv, nV, dptr<int64_t>(c.gs_count), dptr<int64_t>(c.gs_cursor),
+                    dptr<int64_t>(c.gs_bptr), dptr<int32_t>(c.gs_bucket),
+                    dptr<int32_t>(c.gs_ev32), c.scan_tmp.p, c.scan_tmp.cap, c.s);
+}
+
+extern "C" int rsb_dual_graph(int64_t ne, int nv, const int64_t* ev, int64_t* row_ptr,
+                              int32_t* col, int32_t* weight, int64_t cap, int64_t* nnz,
+                              void* stream) {
+  if (!row_ptr || !nnz) return rsb_set_error(RSB_EINVAL, "row_ptr and nnz are needed");
+  Ctx* pc = nullptr;
+  int rc = begin_call(&pc, stream);
+  if (rc) return rc;
+  Ctx& c = *pc;
+  int64_t V = 0;
+  if ((rc = gs_setup(c, ne, nv, ev, &V))) return end_call(c, stream, rc);
+  int* d_flag = (int*)(dptr<unsigned long long>(c.gs_misc) + 1);
+  if ((rc = devbuf_reserve(c.gs_len, sizeof(int64_t) * (size_t)(ne + 2))) ||
+      (rc = devbuf_reserve(c.gs_rowptr, sizeof(int64_t) * (size_t)(ne + 2))))
+    return end_call(c, stream, rc);
+  int64_t* len = dptr<int64_t>(c.gs_len);
+  int64_t* rp = dptr<int64_t>(c.gs_rowptr);
+  const int32_t* ev32 = dptr<int32_t>(c.gs_ev32);
+  const int64_t* bptr = dptr<int64_t>(c.gs_bptr);
+  const int32_t* bucket = dptr<int32_t>(c.gs_bucket);
+  if ((rc = gs_row_lengths(ne, nv, ev32, bptr, bucket, len, d_flag, c.s)))
+    return end_call(c, stream, rc);
+  RSB_CK(cudaMemsetAsync(len + ne, 0, sizeof(int64_t), c.s));
+  if ((rc = launch_scan_i64(len, rp, ne + 1, c.scan_tmp.p, c.scan_tmp.cap, c.s)))
+    return end_call(c, stream, rc);
+  int64_t total = 0;
+  int flag = 0;
+  RSB_CK(cudaMemcpyAsync(&total, rp + ne, sizeof(int64_t), cudaMemcpyDeviceToHost, c.s));
+  RSB_CK(cudaMemcpyAsync(&flag, d_flag, sizeof(int), cudaMemcpyDeviceToHost, c.s));
+  RSB_CK(cudaStreamSynchronize(c.s));
+  if (flag & 2)
+    return end_call(c, stream, rsb_set_error(RSB_EINVAL, "an element meets more than 256 "
+                                                         "other elements at its vertices"));
+  if (flag & 4)
+    return end_call(c, stream, rsb_set_error(RSB_EINVAL, "two elements share more than 7 "
+                                                         "vertices (duplicate elements)"));
+  *nnz = total;
+  RSB_CK(cudaMemcpyAsync(row_ptr, rp, sizeof(int64_t) * (size_t)(ne + 1), cudaMemcpyDefault, c.s));
+  if (col || weight) {
+    if (!col || !weight || cap < total)
+      return end_call(c, stream, rsb_set_error(RSB_EINVAL, "col and weight need room for nnz "
+                                                           "entries (cap < nnz)"));
+    const bool cd = is_device_ptr(col), wd = is_device_ptr(weight);
+    DevBuf tc, tw;
+    int32_t* colp = col;
+    int32_t* wtp = weight;
+    if (!cd && (rc = devbuf_reserve(tc, sizeof(int32_t) * (size_t)std::max<int64_t>(total, 1))))
+      return end_call(c, stream, rc);
+    if (!wd && (rc = devbuf_reserve(tw, sizeof(int32_t) * (size_t)std::max<int64_t>(total, 1)))) {
+      free_buf(tc);
+      return end_call(c, stream, rc);
+    }
+    if (!cd) colp = (int32_t*)tc.p;
+    if (!wd) wtp = (int32_t*)tw.p;
+    rc = gs_fill_dual(ne, nv, ev32, bptr, bucket, rp, colp, wtp, c.s);
+    if (!rc && !cd)
+      if (cudaMemcpyAsync(col, colp, sizeof(int32_t) * total, cudaMemcpyDeviceToHost, c.s))
+        rc = rsb_set_error(RSB_ECUDA, "copy col");
+    if (!rc && !wd)
+      if (cudaMemcpyAsync(weight, wtp, sizeof(int32_t) * total, cudaMemcpyDeviceToHost, c.s))
+        rc = rsb_set_error(RSB_ECUDA, "copy weight");
+    rc = end_call(c, stream, rc);
+    free_buf(tc);
+    free_buf(tw);
+    return rc;
+  }
+  return end_call(c, stream, RSB_OK);
+}
+
+static int gs_lap_common(int64_t ne, int nv, const int64_t* ev, const void* x, void* y, int f32,
+                         int reps, double* ms, double* bytes, void* stream) {
+  Ctx* pc = nullptr;
+  int rc = begin_call(&pc, stream);
+  if (rc) return rc;
+  Ctx& c = *pc;
+  int64_t V = 0;
+  if ((rc = gs_setup(c, ne, nv, ev, &V))) return end_call(c, stream, rc);
+  const size_t es = f32 ? 4 : 8;
+  if ((rc = devbuf_reserve(c.gs_w, es * (size_t)(V + 1)))) return end_call(c, stream, rc);
+  DevBuf tx, ty;
+  const void* xd = x;
+  void* yd = y;
+  if (reps > 0) {  // benchmark: operands of its own
+    if ((rc = devbuf_reserve(tx, es * (size_t)ne)) || (rc = devbuf_reserve(ty, es * (size_t)ne)))
+      return end_call(c, stream, rc);
+    RSB_CK(cudaMemsetAsync(tx.p, 0, es * (size_t)ne, c.s));
+    xd = tx.p;
+    yd = ty.p;
+  } else {
+    if (!is_device_ptr(x)) {
+      if ((rc = devbuf_reserve(tx, es * (size_t)ne))) return end_call(c, stream, rc);
+      RSB_CK(cudaMemcpyAsync(tx.p, x, es * (size_t)ne, cudaMemcpyHostToDevice, c.s));
+      xd = tx.p;
+    }
+    if (!is_device_ptr(y)) {
+      if ((rc = devbuf_reserve(ty, es * (size_t)ne))) return end_call(c, stream, rc);
+      yd = ty.p;
+    }
+  }
+  auto apply = [&]() {
+    return gs_apply(f32, ne, nv, V, dptr<int32_t>(c.gs_ev32), dptr<int64_t>(c.gs_bptr),
+                    dptr<int32_t>(c.gs_bucket), xd, c.gs_w.p, yd, c.s);
+  };
+  if (reps <= 0) {
+    rc = apply();
+    if (!rc && yd != y)
+      if (cudaMemcpyAsync(y, yd, es * (size_t)ne, cudaMemcpyDeviceToHost, c.s))
+        rc = rsb_set_error(RSB_ECUDA, "copy y");
+  } else {
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    for (int w = 0; w < 3 && !rc; ++w) rc = apply();
+    cudaEventRecord(e0, c.s);
+    for (int i = 0; i < reps && !rc; ++i) rc = apply();
+    cudaEventRecord(e1, c.s);
+    cudaEventSynchronize(e1);
+    float t = 0;
+    cudaEventElapsedTime(&t, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (ms) *ms = (double)t / reps;
+    // vertex sums: bucket offsets, bucket entries, x once, w written; element
+    // pass: vertex ids, bucket offsets, w and x read once, y written
+    if (bytes)
+      *bytes = 16.0 * (double)(V + 1) + 8.0 * (double)ne * nv + 3.0 * es * (double)ne +
+               2.0 * es * (double)V;
+  }
+  rc = end_call(c, stream, rc);
+  free_buf(tx);
+  free_buf(ty);
+  return rc;
+}
+
+extern "C" int rsb_laplacian_apply_gs(int64_t ne, int nv, const int64_t* ev, const double* x,
+                                      double* y, void* stream) {
+  if (!x || !y) return rsb_set_error(RSB_EINVAL, "x and y are needed");
+  return gs_lap_common(ne, nv, ev, x, y, 0, 0, nullptr, nullptr, stream);
+}
+
+extern "C" int rsb_laplacian_apply_gs_f32(int64_t ne, int nv, const int64_t* ev, const float* x,
+                                          float* y, void* stream) {
+  if (!x || !y) return rsb_set_error(RSB_EINVAL, "x and y are needed");
+  return gs_lap_common(ne, nv, ev, x, y, 1, 0, nullptr, nullptr, stream);
+}
+
+extern "C" int rsb_laplacian_bench_gs(int64_t ne, int nv, const int64_t* ev, int f32, int reps,
+                                      double* ms_per_apply, double* useful_bytes, void* stream) {
+  if (reps < 1) return rsb_set_error(RSB_EINVAL, "reps");
+  return gs_lap_common(ne, nv, ev, nullptr, nullptr, f32 ? 1 : 0, reps, ms_per_apply,
+                       useful_bytes, stream);
+}
+
 extern "C" const char* rsb_strerror(int code) {
   switch (code) {
     case RSB_OK: return "success";
@@ -1424,11 +1768,14 @@ extern "C" void rsb_release(void) {
                      &c->tiles, &c->sunits, &c->stiles, &c->hist, &c->partials, &c->mom, &c->sbuf,
                      &c->cand[0], &c->cand[1], &c->cand[2], &c->seg_row0, &c->seg_nleft,
                      &c->seg_child0, &c->seg_p0, &c->seg_split, &c->seg_keystar, &c->seg_unit,
-                     &c->seg_ncomp, &c->counters, &c->part_concat};
+                     &c->seg_ncomp, &c->counters, &c->part_concat, &c->blk, &c->coords_cat,
+                     &c->perm, &c->iperm, &c->rcb_home, &c->gs_count, &c->gs_cursor,
+                     &c->gs_bptr, &c->gs_bucket, &c->gs_ev32, &c->gs_len, &c->gs_rowptr,
+                     &c->gs_w, &c->gs_misc};
     for (DevBuf* b : all) free_buf(*b);
     for (int k = 0; k < 2; ++k) {
       PrecBufs& p = c->pb[k];
-      DevBuf* pv[] = {&p.Q, &p.W0, &p.W1, &p.Y, &p.X, &p.R, &p.P, &p.AP};
+      DevBuf* pv[] = {&p.Q, &p.W0, &p.W1, &p.Y, &p.X, &p.R, &p.P, &p.AP, &p.Z0, &p.Z1};
       for (DevBuf* b : pv) free_buf(*b);
     }
     stage_clear(*c);

@@ -50,14 +50,20 @@ int launch_validate(const int64_t* row_ptr, const int32_t* col, const int32_t* w
 // ----------------------------------------------------------------------------
 // SELL-32 ingest
 // ----------------------------------------------------------------------------
-__global__ void k_row_lengths(const int64_t* __restrict__ row_ptr, int64_t n, int32_t* len) {
+// (perm: row i of the new order is row perm[i] of the caller's; NULL = identity)
+__global__ void k_row_lengths(const int64_t* __restrict__ row_ptr, int64_t n, int32_t* len,
+                              const int64_t* __restrict__ perm) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) len[i] = (int32_t)(row_ptr[i + 1] - row_ptr[i]);
+  if (i >= n) return;
+  const int64_t o = perm ? perm[i] : i;
+  len[i] = (int32_t)(row_ptr[o + 1] - row_ptr[o]);
 }
 
-int launch_row_lengths(const int64_t* row_ptr, int64_t n, int32_t* len, cudaStream_t s) {
+int launch_row_lengths(const int64_t* row_ptr, int64_t n, int32_t* len, cudaStream_t s,
+                       const int64_t* perm) {
   if (n <= 0) return RSB_OK;
-  k_row_lengths<<<(unsigned)((n + RSB_BLOCK - 1) / RSB_BLOCK), RSB_BLOCK, 0, s>>>(row_ptr, n, len);
+  k_row_lengths<<<(unsigned)((n + RSB_BLOCK - 1) / RSB_BLOCK), RSB_BLOCK, 0, s>>>(row_ptr, n, len,
+                                                                                  perm);
   RSB_CKL("k_row_lengths");
   return RSB_OK;
 }
@@ -86,7 +92,8 @@ __global__ void k_fill_sell(const int64_t* __restrict__ row_ptr, const int32_t* 
                             int64_t n, int64_t row_off, int64_t home_off, int32_t seg,
                             const int64_t* __restrict__ slice_ptr, uint32_t* __restrict__ ent,
                             int32_t* __restrict__ deg, int64_t* __restrict__ gid,
-                            int64_t* __restrict__ home, int32_t* __restrict__ row_seg) {
+                            int64_t* __restrict__ home, int32_t* __restrict__ row_seg,
+                            const int64_t* __restrict__ perm, const int32_t* __restrict__ iperm) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const int64_t r = row_off + i;
@@ -94,29 +101,32 @@ __global__ void k_fill_sell(const int64_t* __restrict__ row_ptr, const int32_t* 
   const int lane = (int)(r & 31);
   const int64_t base = slice_ptr[sl];
   const int width = (int)((slice_ptr[sl + 1] - base) >> 5);
-  const int64_t b = row_ptr[i], e = row_ptr[i + 1];
+  const int64_t o = perm ? perm[i] : i;  // the caller's row
+  const int64_t b = row_ptr[o], e = row_ptr[o + 1];
   int k = 0, d = 0;
   for (int64_t p = b; p < e; ++p, ++k) {
     const uint32_t w = wt ? (uint32_t)wt[p] : 1u;
-    ent[base + 32ll * k + lane] = (w << RSB_COLBITS) | (uint32_t)(col[p] + row_off);
+    const int64_t c = iperm ? (int64_t)iperm[col[p]] : (int64_t)col[p];
+    ent[base + 32ll * k + lane] = (w << RSB_COLBITS) | (uint32_t)(c + row_off);
     d += (int)w;
   }
   for (; k < width; ++k) ent[base + 32ll * k + lane] = (uint32_t)r;  // weight 0, own column
   // the per-row arrays are optional (NULL: not wanted by the caller)
   if (deg) deg[r] = d;
-  if (gid) gid[r] = gid_in ? gid_in[i] : i;
-  if (home) home[r] = home_off + i;
+  if (gid) gid[r] = gid_in ? gid_in[o] : o;
+  if (home) home[r] = home_off + o;
   if (row_seg) row_seg[r] = seg;
 }
 
 int launch_fill_sell(const int64_t* row_ptr, const int32_t* col, const int32_t* wt,
                      const int64_t* gid_in, int64_t n, int64_t row_off, int64_t home_off,
                      int32_t seg, const int64_t* slice_ptr, uint32_t* ent, int32_t* deg,
-                     int64_t* gid, int64_t* home, int32_t* row_seg, cudaStream_t s) {
+                     int64_t* gid, int64_t* home, int32_t* row_seg, cudaStream_t s,
+                     const int64_t* perm, const int32_t* iperm) {
   if (n <= 0) return RSB_OK;
   k_fill_sell<<<(unsigned)((n + RSB_BLOCK - 1) / RSB_BLOCK), RSB_BLOCK, 0, s>>>(
       row_ptr, col, wt, gid_in, n, row_off, home_off, seg, slice_ptr, ent, deg, gid, home,
-      row_seg);
+      row_seg, perm, iperm);
   RSB_CKL("k_fill_sell");
   return RSB_OK;
 }
@@ -212,17 +222,8 @@ __global__ void __launch_bounds__(RSB_BLOCK) k_spmv(const int64_t* __restrict__ 
   const int r = blockIdx.x * RSB_BLOCK + threadIdx.x;
   int width = 0;
   if (r < n) {
-    const int64_t base = slice_ptr[r >> 5];
-    width = (int)((slice_ptr[(r >> 5) + 1] - base) >> 5);
-    const uint32_t* e = ent + base + (r & 31);
-    const V xr = x[r];
-    V acc = V(0);
-#pragma unroll 4
-    for (int k = 0; k < width; ++k) {
-      const uint32_t p = __ldg(e + 32 * k);
-      acc += V(ent_w(p)) * (xr - __ldg(x + ent_col(p)));
-    }
-    y[r] = acc;
+    width = (int)((slice_ptr[(r >> 5) + 1] - slice_ptr[r >> 5]) >> 5);
+    y[r] = spmv_row_ro<V>(slice_ptr, ent, x, r, __ldg(x + r));
   }
   if (pbytes) {  // algorithmic bytes: entries, x once, y once
     unsigned long long b = r < n ? 4ull * width + 2ull * sizeof(V) : 0ull;
@@ -530,5 +531,81 @@ int launch_write_parts(const LevelGraph& G, const int32_t* seg_p0, int32_t* part
   k_write_parts<<<(G.n + RSB_BLOCK - 1) / RSB_BLOCK, RSB_BLOCK, 0, s>>>(G.home, G.row_seg, G.n,
                                                                         seg_p0, part_concat);
   RSB_CKL("k_write_parts");
+  return RSB_OK;
+}
+
+// ----------------------------------------------------------------------------
+// recursive coordinate bisection: the coordinate of every unit row along the
+// axis of the unit's largest coordinate extent (the lowest axis on equal
+// extents); coords are the caller's (x, y, z) per element, indexed by home
+// ----------------------------------------------------------------------------
+__global__ void __launch_bounds__(RSB_BLOCK)
+    k_rcb_box(const Tile* __restrict__ tiles, Unit* units, const int64_t* __restrict__ home,
+              const double* __restrict__ coords, double* partials, long long stride) {
+  __shared__ double sm[6][RSB_WARPS];
+  __shared__ double out[6];
+  const Tile t = tiles[blockIdx.x];
+  Unit& u = units[t.unit];
+  if (!u.valid) return;
+  double m[6];
+#pragma unroll
+  for (int a = 0; a < 6; ++a) m[a] = -1e300;
+  for (int r = t.row0 + threadIdx.x; r < t.row1; r += RSB_BLOCK) {
+    const double* c = coords + 3 * home[r];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      m[a] = fmax(m[a], c[a]);
+      m[3 + a] = fmax(m[3 + a], -c[a]);
+    }
+  }
+#pragma unroll
+  for (int a = 0; a < 6; ++a) {
+    const double w = warp_max(m[a]);
+    if ((threadIdx.x & 31) == 0) sm[a][threadIdx.x >> 5] = w;
+  }
+  __syncthreads();
+  if (threadIdx.x < 6) {
+    double b = -1e300;
+    for (int i = 0; i < RSB_WARPS; ++i) b = fmax(b, sm[threadIdx.x][i]);
+    partials[(long long)threadIdx.x * stride + blockIdx.x] = b;
+  }
+  if (last_cta(&u.cnt, u.ntile)) {
+    if (threadIdx.x < 6) {
+      double b = -1e300;
+      for (int i = 0; i < u.ntile; ++i)
+        b = fmax(b, __ldcg(partials + threadIdx.x * stride + u.tile0 + i));
+      out[threadIdx.x] = b;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      int ax = 0;
+      double best = out[0] + out[3];
+      for (int a = 1; a < 3; ++a)
+        if (out[a] + out[3 + a] > best) {
+          best = out[a] + out[3 + a];
+          ax = a;
+        }
+      u.axis = ax;
+    }
+  }
+}
+
+__global__ void k_rcb_vec(const Tile* __restrict__ tiles, const Unit* units,
+                          const int64_t* __restrict__ home, const double* __restrict__ coords,
+                          double* v) {
+  const Tile t = tiles[blockIdx.x];
+  const Unit& u = units[t.unit];
+  if (!u.valid) return;
+  const int ax = u.axis;
+  for (int r = t.row0 + threadIdx.x; r < t.row1; r += RSB_BLOCK) v[r] = coords[3 * home[r] + ax];
+}
+
+int launch_rcb_vector(const LevelGraph& G, const Tile* tiles, int ntiles, Unit* units,
+                      const double* coords, double* v, double* partials, cudaStream_t s) {
+  if (ntiles <= 0) return RSB_OK;
+  k_rcb_box<<<ntiles, RSB_BLOCK, 0, s>>>(tiles, units, G.home, coords, partials, ntiles);
+  RSB_CKL("k_rcb_box");
+  k_rcb_vec<<<ntiles, RSB_BLOCK, 0, s>>>(tiles, units, G.home, coords, v);
+  RSB_CKL("k_rcb_vec");
   return RSB_OK;
 }

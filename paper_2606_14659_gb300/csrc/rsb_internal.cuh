@@ -107,7 +107,7 @@ struct Unit {
   int32_t best;
   int32_t ncand;
   unsigned int cnt;      // last-CTA counter of the segmented reductions
-  int32_t pad1;
+  int32_t axis;          // RCB: coordinate axis of the split
 };
 
 struct Tile {
@@ -177,6 +177,34 @@ __device__ __forceinline__ uint64_t dkey(double v) {
 __device__ __forceinline__ double dkey_inv(uint64_t k) {
   const uint64_t b = (k >> 63) ? (k & 0x7FFFFFFFFFFFFFFFull) : ~k;
   return __longlong_as_double((long long)b);
+}
+
+// Laplacian action of one row, y_r = sum_k w_rk (x_r - x_{c_k}) in entry order
+// (the order every other form of the action uses, so the results are the same
+// bit for bit), for x that no thread of the launch writes: the row's entries
+// are loaded eight at a time and their gathers issued together through the
+// read-only path, so each thread keeps up to eight gathers in flight.
+// Entries past the row's width are neither loaded nor gathered.
+template <typename V>
+__device__ __forceinline__ V spmv_row_ro(const int64_t* __restrict__ slice_ptr,
+                                         const uint32_t* __restrict__ ent,
+                                         const V* __restrict__ x, int r, V xr) {
+  const int64_t base = slice_ptr[r >> 5];
+  const int width = (int)((slice_ptr[(r >> 5) + 1] - base) >> 5);
+  const uint32_t* e = ent + base + (r & 31);
+  V acc = V(0);
+  for (int k0 = 0; k0 < width; k0 += 8) {
+    uint32_t p[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) p[i] = k0 + i < width ? __ldg(e + 32 * (k0 + i)) : 0u;
+    V xv[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) xv[i] = k0 + i < width ? __ldg(x + ent_col(p[i])) : xr;
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+      if (k0 + i < width) acc += V(ent_w(p[i])) * (xr - xv[i]);
+  }
+  return acc;
 }
 
 // Row membership in a unit.
@@ -378,6 +406,68 @@ __device__ __forceinline__ void final_reduce(const double* partials, long long s
   __syncthreads();
 }
 
+// ----------------------------------------------------------------------------
+// mbarrier and 1-D bulk copies (cp.async.bulk global -> shared, completion
+// counted in bytes on an mbarrier); every wait is bounded by the global timer
+// ----------------------------------------------------------------------------
+__device__ __forceinline__ unsigned smem_addr(const void* p) {
+  return (unsigned)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity,
+                                                  unsigned long long limit_ns) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const unsigned long long t0 = global_ns();
+  while (!mbar_try_wait(bar, parity))
+    if (global_ns() - t0 > limit_ns) return false;
+  return true;
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes,
+                                         uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+          "r"(smem_addr(dst)),
+      "l"(src), "r"(bytes), "r"(smem_addr(bar))
+      : "memory");
+}
+
+// All threads: wait for chunk ci (buffer ci & 1); false (uniform) when the
+// copies did not complete in time, after flagging the grid error word and
+// draining this CTA's copies still in flight (chunks ci and ci + 1).
+__device__ __forceinline__ bool bulk_wait_chunk(uint64_t* bar, int ci, int nchunk, GridBar* gb) {
+  const bool ok = mbar_wait_bounded(&bar[ci & 1], (ci >> 1) & 1, 2000000000ull);
+  if (!__syncthreads_or(!ok)) return true;
+  if (threadIdx.x == 0) {
+    atomicMax(&gb->err, 1);
+    // drain this CTA's copies still in flight before the CTA exits; if even
+    // that runs out, the error word says so (2) and the call reports it
+    bool drained = mbar_wait_bounded(&bar[ci & 1], (ci >> 1) & 1, 1000000000ull);
+    if (ci + 1 < nchunk)
+      drained = mbar_wait_bounded(&bar[(ci + 1) & 1], ((ci + 1) >> 1) & 1, 1000000000ull) &&
+                drained;
+    if (!drained) atomicMax(&gb->err, 2);
+  }
+  __syncthreads();
+  return false;
+}
+
 #endif  // __CUDACC__
 
 // ----------------------------------------------------------------------------
@@ -449,12 +539,16 @@ static inline T* dptr(DevBuf& b) {
 // ----------------------------------------------------------------------------
 int launch_validate(const int64_t* row_ptr, const int32_t* col, const int32_t* wt, int64_t n,
                     int symmetric, int* flag, cudaStream_t s);
-int launch_row_lengths(const int64_t* row_ptr, int64_t n, int32_t* len, cudaStream_t s);
+int launch_row_lengths(const int64_t* row_ptr, int64_t n, int32_t* len, cudaStream_t s,
+                       const int64_t* perm = nullptr);
 int launch_slice_widths(const int32_t* len, int64_t n, int64_t* slice_sz, cudaStream_t s);
 int launch_fill_sell(const int64_t* row_ptr, const int32_t* col, const int32_t* wt,
                      const int64_t* gid_in, int64_t n, int64_t row_off, int64_t home_off,
                      int32_t seg, const int64_t* slice_ptr, uint32_t* ent, int32_t* deg,
-                     int64_t* gid, int64_t* home, int32_t* row_seg, cudaStream_t s);
+                     int64_t* gid, int64_t* home, int32_t* row_seg, cudaStream_t s,
+                     const int64_t* perm = nullptr, const int32_t* iperm = nullptr);
+int launch_rcb_vector(const LevelGraph& G, const Tile* tiles, int ntiles, Unit* units,
+                      const double* coords, double* v, double* partials, cudaStream_t s);
 int launch_scan_i64(const int64_t* in, int64_t* out_excl, int64_t n, void* tmp, size_t tmp_bytes,
                     cudaStream_t s);
 size_t scan_tmp_bytes(int64_t n);
@@ -495,6 +589,9 @@ struct SolveBufs {
   struct GridBar* gb = nullptr;  // barrier of the persistent cycle kernel
   double* S = nullptr;           // per-unit projected matrices and Ritz vectors
   int* jmin = nullptr;           // device: smallest next-cycle start step (2 slots)
+  void* Z0 = nullptr;            // block Lanczos: interleaved residual blocks (4 values/row)
+  void* Z1 = nullptr;
+  void* bu = nullptr;            // block Lanczos: per-unit block state
   int64_t N = 0;
   int trmax = 0;                 // largest tile of the level, rows
   int maxcycles = 0;             // cycle cap of the current solve

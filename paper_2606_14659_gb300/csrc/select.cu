@@ -116,7 +116,7 @@ __global__ void __launch_bounds__(RSB_BLOCK)
 __global__ void __launch_bounds__(RSB_BLOCK)
     k_orient_gstar(const int64_t* __restrict__ gid, const Tile* __restrict__ tiles, Unit* units,
                    const uint64_t* __restrict__ ckey, const double* __restrict__ v, int cand,
-                   double tie_rel, double* partials, long long stride) {
+                   double tie_rel, double* partials, long long stride, int fixed_sign) {
   __shared__ long long smg[RSB_WARPS];
   __shared__ double smv[RSB_WARPS];
   const Tile t = tiles[blockIdx.x];
@@ -159,20 +159,21 @@ __global__ void __launch_bounds__(RSB_BLOCK)
       }
       u.gstar = (int64_t)bg;
       u.gstar_v = bv;
-      u.sign = bv > 0.0 ? -1.0 : 1.0;
+      u.sign = fixed_sign ? 1.0 : (bv > 0.0 ? -1.0 : 1.0);
       u.tau = tie_rel * (u.vmax - u.vmin);
     }
   }
 }
 
+// fixed_sign: keep v as it is (RCB: lower coordinates go left)
 int launch_orient(const LevelGraph& G, const Tile* tiles, int ntiles, Unit* units,
                   const uint64_t* ckey, const double* v, int cand, double tie_rel,
-                  double* partials, cudaStream_t s) {
+                  double* partials, cudaStream_t s, int fixed_sign) {
   if (ntiles <= 0) return RSB_OK;
   k_orient_stats<<<ntiles, RSB_BLOCK, 0, s>>>(tiles, units, ckey, v, cand, partials, ntiles);
   RSB_CKL("k_orient_stats");
   k_orient_gstar<<<ntiles, RSB_BLOCK, 0, s>>>(G.gid, tiles, units, ckey, v, cand, tie_rel,
-                                              partials, ntiles);
+                                              partials, ntiles, fixed_sign);
   RSB_CKL("k_orient_gstar");
   return RSB_OK;
 }

@@ -422,44 +422,6 @@ __global__ void __launch_bounds__(RSB_BLOCK) k_lz_c(LzArgs<V> a, int j, double b
 // the global timer): on timeout the CTA sets the grid error word, waits
 // (bounded) for its own copies still in flight and returns.
 // ----------------------------------------------------------------------------
-__device__ __forceinline__ unsigned smem_addr(const void* p) {
-  return (unsigned)__cvta_generic_to_shared(p);
-}
-__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
-               "r"(bytes)
-               : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
-  unsigned ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-      " selp.u32 %0, 1, 0, p;\n}"
-      : "=r"(ok)
-      : "r"(smem_addr(bar)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity,
-                                                  unsigned long long limit_ns) {
-  if (mbar_try_wait(bar, parity)) return true;
-  const unsigned long long t0 = global_ns();
-  while (!mbar_try_wait(bar, parity))
-    if (global_ns() - t0 > limit_ns) return false;
-  return true;
-}
-__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes,
-                                         uint64_t* bar) {
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
-          "r"(smem_addr(dst)),
-      "l"(src), "r"(bytes), "r"(smem_addr(bar))
-      : "memory");
-}
-
 template <typename V>
 struct BulkRows {
   static constexpr int AL = 16 / sizeof(V);        // rows per 16 bytes
@@ -490,22 +452,6 @@ __device__ __forceinline__ void bulk_issue_chunk(const LzArgs<V>& a, V* Qb, uint
   for (int k = 0; k < nq; ++k)
     bulk_g2s(dst + (size_t)k * CRB, a.Q + (long long)k * a.N + a0, bytes, &bar[b]);
   if (extra) bulk_g2s(dst + (size_t)nq * CRB, extra + a0, bytes, &bar[b]);
-}
-
-// All threads: wait for chunk ci (buffer ci & 1); false (uniform) when the
-// copies did not complete in time, after flagging the grid error word and
-// draining this CTA's copies still in flight (chunks ci and ci + 1).
-__device__ __forceinline__ bool bulk_wait_chunk(uint64_t* bar, int ci, int nchunk, GridBar* gb) {
-  const bool ok = mbar_wait_bounded(&bar[ci & 1], (ci >> 1) & 1, 2000000000ull);
-  if (!__syncthreads_or(!ok)) return true;
-  if (threadIdx.x == 0) {
-    atomicExch(&gb->err, 1);
-    mbar_wait_bounded(&bar[ci & 1], (ci >> 1) & 1, 1000000000ull);
-    if (ci + 1 < nchunk)
-      mbar_wait_bounded(&bar[(ci + 1) & 1], ((ci + 1) >> 1) & 1, 1000000000ull);
-  }
-  __syncthreads();
-  return false;
 }
 
 template <typename V>
@@ -614,7 +560,7 @@ __global__ void __launch_bounds__(RSB_BLOCK) k_lz_a1(LzArgs<V> a, int j) {
 #pragma unroll 4
   for (int r = t.row0 + threadIdx.x; r < t.row1; r += RSB_BLOCK) {
     const V xr = src[r];
-    dst[r] = s * spmv_row<V, false>(a.slice_ptr, a.ent, src, r, xr);
+    dst[r] = s * spmv_row_ro<V>(a.slice_ptr, a.ent, src, r, xr);
     qj[r] = s * xr;
     if (a.pb_a) pbytes += 4ull * row_width(a.slice_ptr, r) + 3ull * sizeof(V);
   }
@@ -877,6 +823,14 @@ __global__ void __launch_bounds__(RSB_BLOCK) k_lz_eig(Unit* units, double* S, in
   __shared__ JacShared<T> J;
   if ((int)blockIdx.x >= nunits) return;
   lz_eig_u<T, false>(units[blockIdx.x], unit_S(S, blockIdx.x), J);
+}
+
+// The Ritz-pair launch for other solvers of the library (block Lanczos).
+int launch_lz_eig(int f32, Unit* units, double* S, int nunits, cudaStream_t s) {
+  if (f32) k_lz_eig<float><<<nunits, RSB_BLOCK, 0, s>>>(units, S, nunits);
+  else k_lz_eig<double><<<nunits, RSB_BLOCK, 0, s>>>(units, S, nunits);
+  RSB_CKL("k_lz_eig");
+  return RSB_OK;
 }
 
 // ----------------------------------------------------------------------------
@@ -1458,14 +1412,18 @@ __global__ void __launch_bounds__(RSB_BLOCK) k_start(LzArgs<V> a, uint64_t sd, c
 // mode: number of deflation vectors nd (0, 1, 2).  A unit joins the solve when
 // it is valid, its space orthogonal to 1 and the deflation vectors is not
 // empty, and (nd > 0) it found a cluster of size nd so far.
+// Units whose dimension dim = n - 1 - nd lies outside [dim_lo, dim_hi] are left
+// as they are (another solver takes them).
 __global__ void k_solve_init(Unit* units, int nunits, int nd, int krylov, int maxcycles, double tol,
-                             int require_cluster, int keep, int* n_active) {
+                             int require_cluster, int keep, long long dim_lo, long long dim_hi,
+                             int* n_active) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= nunits) return;
   Unit& u = units[i];
+  const long long dim = u.n - 1 - nd;
+  if (u.valid && dim > 0 && (dim < dim_lo || dim > dim_hi)) return;
   u.status = U_IDLE;
   if (!u.valid) return;
-  const long long dim = u.n - 1 - nd;
   if (dim <= 0) return;
   if (require_cluster && u.ncand != nd) return;
   u.nd = nd;
@@ -1524,11 +1482,13 @@ static LzArgs<V> make_args(const LevelGraph& G, const Tile* tiles, int ntiles, U
 }
 
 int solver_setup(Unit* units, int nunits, int nd, int krylov, int maxcycles, double tol,
-                 int require_cluster, int keep, SolveBufs& B, cudaStream_t s) {
+                 int require_cluster, int keep, SolveBufs& B, cudaStream_t s, long long dim_lo,
+                 long long dim_hi) {
   B.maxcycles = maxcycles;
   RSB_CK(cudaMemsetAsync(B.n_active, 0, sizeof(int), s));
   k_solve_init<<<(nunits + 127) / 128, 128, 0, s>>>(units, nunits, nd, krylov, maxcycles, tol,
-                                                    require_cluster, keep, B.n_active);
+                                                    require_cluster, keep, dim_lo, dim_hi,
+                                                    B.n_active);
   RSB_CKL("k_solve_init");
   return RSB_OK;
 }
@@ -1540,7 +1500,11 @@ static int read_active(SolveBufs& B, cudaStream_t s, int* out) {
   RSB_CK(cudaStreamSynchronize(s));
   prof_collect();
   *out = *B.h_active;
-  if (B.gb && B.h_active[1]) return rsb_set_error(RSB_ETIMEOUT, "grid barrier wait gave up");
+  if (B.gb && B.h_active[1] == 2)
+    return rsb_set_error(RSB_ETIMEOUT,
+                         "a bounded device wait gave up and a CTA's bulk copies in flight did "
+                         "not drain before it exited");
+  if (B.gb && B.h_active[1]) return rsb_set_error(RSB_ETIMEOUT, "a bounded device wait gave up");
   return RSB_OK;
 }
 
@@ -1785,7 +1749,7 @@ __global__ void __launch_bounds__(RSB_BLOCK) k_cg_ap(LzArgs<V> a) {
   unsigned long long pbytes = 0;
   for (int r = t.row0 + threadIdx.x; r < t.row1; r += RSB_BLOCK) {
     const V pr = a.P[r];
-    const V ap = spmv_row<V>(a.slice_ptr, a.ent, a.P, r, pr);
+    const V ap = spmv_row_ro<V>(a.slice_ptr, a.ent, a.P, r, pr);
     a.AP[r] = ap;
     acc.add(pr * ap);
     if (a.pb_cg) pbytes += 4ull * row_width(a.slice_ptr, r) + 2ull * sizeof(V);
@@ -1879,7 +1843,7 @@ __global__ void __launch_bounds__(RSB_BLOCK) k_inv_rq(LzArgs<V> a) {
   Acc<V> yly, yy;
   for (int r = t.row0 + threadIdx.x; r < t.row1; r += RSB_BLOCK) {
     const V yr = a.X[r];
-    const V ly = spmv_row<V>(a.slice_ptr, a.ent, a.X, r, yr);
+    const V ly = spmv_row_ro<V>(a.slice_ptr, a.ent, a.X, r, yr);
     a.AP[r] = ly;
     yly.add(yr * ly);
     yy.add(yr * yr);

@@ -17,7 +17,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_lib", "librsb.so")
 
 RSB_OK, RSB_EINVAL, RSB_ENOMEM, RSB_ECUDA, RSB_ENOCONV, RSB_ETIMEOUT, RSB_EDISCONNECTED = range(7)
-RSB_LANCZOS, RSB_INVERSE = 0, 1
+RSB_LANCZOS, RSB_INVERSE, RSB_RCB = 0, 1, 2
 RSB_FP64, RSB_MIXED = 0, 1
 RSB_DEGEN_NONE, RSB_DEGEN_RESOLVE = 0, 1
 
@@ -25,7 +25,8 @@ EXPORTED = ["rsb_options_default", "rsb_partition", "rsb_partition_batch", "rsb_
             "rsb_laplacian_apply", "rsb_laplacian_apply_f32", "rsb_laplacian_bench",
             "rsb_strerror", "rsb_last_error_detail", "rsb_release", "rsb_profile_begin",
             "rsb_profile_end", "rsb_laplacian_apply_noalloc", "rsb_autotune",
-            "rsb_test_poison_barrier", "rsb_profile_read"]
+            "rsb_test_poison_barrier", "rsb_profile_read", "rsb_dual_graph",
+            "rsb_laplacian_apply_gs", "rsb_laplacian_apply_gs_f32", "rsb_laplacian_bench_gs"]
 
 RSB_TUNE_CANDIDATES = 6
 TUNE_CANDIDATES = [(2, 3), (4, 3), (8, 3), (2, 1), (4, 1), (8, 1)]  # (tile_rows, use_graph)
@@ -33,7 +34,7 @@ TUNE_CANDIDATES = [(2, 3), (4, 3), (8, 3), (2, 1), (4, 1), (8, 1)]  # (tile_rows
 
 class rsb_csr(C.Structure):
     _fields_ = [("n", C.c_int64), ("row_ptr", C.c_void_p), ("col", C.c_void_p),
-                ("weight", C.c_void_p), ("gid", C.c_void_p)]
+                ("weight", C.c_void_p), ("gid", C.c_void_p), ("coords", C.c_void_p)]
 
 
 class rsb_options(C.Structure):
@@ -43,7 +44,8 @@ class rsb_options(C.Structure):
                 ("degenerate_policy", C.c_int), ("cluster_tol", C.c_double),
                 ("tie_rel", C.c_double), ("mixed_tol", C.c_double), ("batched", C.c_int),
                 ("use_graph", C.c_int), ("validate", C.c_int), ("polish_cycles", C.c_int),
-                ("keep", C.c_int), ("tile_rows", C.c_int), ("polish_dim", C.c_int)]
+                ("keep", C.c_int), ("tile_rows", C.c_int), ("polish_dim", C.c_int),
+                ("block", C.c_int), ("reorder", C.c_int)]
 
 
 class rsb_stats(C.Structure):
@@ -85,6 +87,12 @@ def load():
                                         C.POINTER(C.c_double), C.POINTER(C.c_double), vp]
     lib.rsb_autotune.argtypes = [C.POINTER(rsb_csr), C.c_int32, C.POINTER(C.c_int32),
                                  C.POINTER(rsb_options), C.POINTER(vp), C.POINTER(C.c_double), vp]
+    lib.rsb_dual_graph.argtypes = [C.c_int64, C.c_int, vp, vp, vp, vp, C.c_int64,
+                                   C.POINTER(C.c_int64), vp]
+    lib.rsb_laplacian_apply_gs.argtypes = [C.c_int64, C.c_int, vp, vp, vp, vp]
+    lib.rsb_laplacian_apply_gs_f32.argtypes = [C.c_int64, C.c_int, vp, vp, vp, vp]
+    lib.rsb_laplacian_bench_gs.argtypes = [C.c_int64, C.c_int, vp, C.c_int, C.c_int,
+                                           C.POINTER(C.c_double), C.POINTER(C.c_double), vp]
     lib.rsb_test_poison_barrier.argtypes = [C.c_int]
     lib.rsb_test_poison_barrier.restype = None
     lib.rsb_strerror.argtypes = [C.c_int]
@@ -103,7 +111,9 @@ def load():
     lib.rsb_profile_read.restype = None
     for name in ("rsb_partition", "rsb_partition_batch", "rsb_fiedler", "rsb_autotune",
                  "rsb_laplacian_apply",
-                 "rsb_laplacian_apply_f32", "rsb_laplacian_bench", "rsb_laplacian_apply_noalloc"):
+                 "rsb_laplacian_apply_f32", "rsb_laplacian_bench", "rsb_laplacian_apply_noalloc",
+                 "rsb_dual_graph", "rsb_laplacian_apply_gs", "rsb_laplacian_apply_gs_f32",
+                 "rsb_laplacian_bench_gs"):
         getattr(lib, name).restype = C.c_int
     _lib = lib
     return lib
@@ -139,10 +149,11 @@ class Graph:
     weight: object
     gid: object
     device: str
+    coords: object = None
 
     def c_struct(self) -> rsb_csr:
         return rsb_csr(self.n, _ptr(self.row_ptr), _ptr(self.col), _ptr(self.weight),
-                       _ptr(self.gid))
+                       _ptr(self.gid), _ptr(self.coords))
 
 
 def _ptr(a):
@@ -153,31 +164,39 @@ def _ptr(a):
     return a.data_ptr()
 
 
-def graph(g, device: str = "cuda", gid: bool = True) -> Graph:
+def graph(g, device: str = "cuda", gid: bool = True, coords=None) -> Graph:
     """Wraps a meshgen.DualGraph (or anything with n/row_ptr/col/w/gid) for the ABI.
 
     device="cuda": arrays are copied to the current GPU as torch tensors;
     device="host": numpy arrays are passed and the library copies them itself.
+    coords: n x 3 element coordinates; by default the centroids of a box mesh
+    when the graph has them.
     """
     rp = np.ascontiguousarray(g.row_ptr, dtype=np.int64)
     col = np.ascontiguousarray(g.col, dtype=np.int32)
     w = None if getattr(g, "w", None) is None else np.ascontiguousarray(g.w, dtype=np.int32)
     gd = np.ascontiguousarray(g.gid, dtype=np.int64) if gid and g.gid is not None else None
+    if coords is None and hasattr(g, "centroids") and getattr(g, "dims", None) is not None:
+        try:
+            coords = g.centroids()
+        except ValueError:
+            coords = None
+    xyz = None if coords is None else np.ascontiguousarray(coords, dtype=np.float64).reshape(-1)
     if device == "host":
-        return Graph(int(g.n), rp, col, w, gd, "host")
+        return Graph(int(g.n), rp, col, w, gd, "host", xyz)
     import torch
 
     def t(a):
         return None if a is None else torch.from_numpy(a).to(device)
 
-    return Graph(int(g.n), t(rp), t(col), t(w), t(gd), device)
+    return Graph(int(g.n), t(rp), t(col), t(w), t(gd), device, t(xyz))
 
 
 def options(**kw) -> rsb_options:
     """rsb_options with the library defaults, overridden by keyword."""
     o = rsb_options()
     load().rsb_options_default(C.byref(o))
-    names = {"method": {"lanczos": RSB_LANCZOS, "inverse": RSB_INVERSE},
+    names = {"method": {"lanczos": RSB_LANCZOS, "inverse": RSB_INVERSE, "rcb": RSB_RCB},
              "precision": {"fp64": RSB_FP64, "mixed": RSB_MIXED},
              "degenerate_policy": {"none": RSB_DEGEN_NONE, "resolve": RSB_DEGEN_RESOLVE}}
     for k, v in kw.items():
@@ -326,6 +345,56 @@ def rsb_laplacian_bench(g: Graph, f32: bool, reps: int = 20, stream=None):
     by = C.c_double(0.0)
     _check(lib.rsb_laplacian_bench(C.byref(cs), int(bool(f32)), int(reps), C.byref(ms),
                                    C.byref(by), _stream(stream)), "rsb_laplacian_bench")
+    return ms.value, by.value
+
+
+def rsb_dual_graph(ev, device: str = "cuda", stream=None):
+    """Dual graph (n, row_ptr, col, weight) of elements given by their vertex
+    ids ev (ne x nv integer array or tensor); arrays on `device` ("cuda" or
+    "host")."""
+    lib = load()
+    import torch
+
+    evt = ev if not isinstance(ev, np.ndarray) else torch.from_numpy(
+        np.ascontiguousarray(ev, dtype=np.int64))
+    if device != "host":
+        evt = evt.to(device)
+    ne, nv = int(evt.shape[0]), int(evt.shape[1])
+    dev = "cpu" if device == "host" else device
+    rp = torch.empty(ne + 1, dtype=torch.int64, device=dev)
+    nnz = C.c_int64(0)
+    st = _stream(stream)
+    _check(lib.rsb_dual_graph(ne, nv, _ptr(evt), _ptr(rp), None, None, 0, C.byref(nnz), st),
+           "rsb_dual_graph")
+    col = torch.empty(max(nnz.value, 1), dtype=torch.int32, device=dev)
+    w = torch.empty(max(nnz.value, 1), dtype=torch.int32, device=dev)
+    _check(lib.rsb_dual_graph(ne, nv, _ptr(evt), _ptr(rp), _ptr(col), _ptr(w), nnz.value,
+                              C.byref(nnz), st), "rsb_dual_graph")
+    return ne, rp, col[:nnz.value], w[:nnz.value]
+
+
+def rsb_laplacian_apply_gs(ev, x, y=None, stream=None):
+    """y = L x by gather-scatter from the element -> vertex ids (precision of x)."""
+    lib = load()
+    import torch
+
+    f32 = str(x.dtype) == "torch.float32"
+    if y is None:
+        y = torch.empty_like(x)
+    fn = lib.rsb_laplacian_apply_gs_f32 if f32 else lib.rsb_laplacian_apply_gs
+    _check(fn(int(ev.shape[0]), int(ev.shape[1]), _ptr(ev), _ptr(x), _ptr(y), _stream(stream)),
+           "rsb_laplacian_apply_gs")
+    return y
+
+
+def rsb_laplacian_bench_gs(ev, f32: bool, reps: int = 20, stream=None):
+    """(mean ms per gather-scatter Laplacian, algorithmic bytes per application)."""
+    lib = load()
+    ms = C.c_double(0.0)
+    by = C.c_double(0.0)
+    _check(lib.rsb_laplacian_bench_gs(int(ev.shape[0]), int(ev.shape[1]), _ptr(ev),
+                                      int(bool(f32)), int(reps), C.byref(ms), C.byref(by),
+                                      _stream(stream)), "rsb_laplacian_bench_gs")
     return ms.value, by.value
 
 

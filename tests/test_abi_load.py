@@ -48,7 +48,8 @@ def test_binding_struct_layout_and_strerror():
     import paper_2606_14659_gb300.rsb as R
 
     lib = R.load()
-    assert ctypes.sizeof(R.rsb_options) == 112
+    assert ctypes.sizeof(R.rsb_options) == 120 and R.rsb_options.block.offset == 108
+    assert R.rsb_options.reorder.offset == 112 and ctypes.sizeof(R.rsb_csr) == 48
     assert R.rsb_options.keep.offset == 96 and R.rsb_options.tile_rows.offset == 100
     assert R.rsb_options.polish_dim.offset == 104
     assert R.rsb_options.polish_cycles.offset == 92 and R.rsb_options.seed.offset == 40

@@ -2,18 +2,26 @@
 
 * C3: 192x128x96 box, 10% seeded deletion, largest component, vertex adjacency
   (4/2/1), inverse iteration with CG (FP32 vectors, FP64 alpha/beta), 256 parts;
-  the FP32 vector is polished by FP64 Lanczos cycles (on 26-neighbour graphs
-  the Rayleigh quotient of an FP32-accurate vector alone misses the 1e-6
-  bound on lambda_2).
+  the first two levels are compared with the oracle's own lambda_2 and cuts
+  (stored by tests/golden/make_golden.py); the FP32 vector is polished by FP64
+  Lanczos cycles (on 26-neighbour graphs the Rayleigh quotient of an
+  FP32-accurate vector alone misses the 1e-6 bound on lambda_2).
 * C4: 512 boxes with sides drawn from [8, 96], face adjacency, 16 parts each, one
   batched call per level.
 * C5: 256^3 box, 5% deletion, vertex adjacency, mixed Lanczos, 1024 parts.
+  Its first split has lambda_2..lambda_4 within a fraction of a percent (a cube
+  with random deletions): within the paper's cap of 50 restarts no solver here,
+  the FP64 oracle included, reaches a residual at which lambda_2 is fixed to
+  1e-6, so C5 is checked by sizes, the residual bar and quality only.
 
 At these sizes the oracle checks sampled outputs one by one: it applies its own
 Laplacian to the library's Fiedler vector (residual and Rayleigh quotient), it
 fixes the exact part sizes (R6), and it partitions small meshes of the C4 batch
 completely.  Closed-form meshes of the batch must match bit for bit.
 """
+import json
+import os
+
 import numpy as np
 import pytest
 
@@ -53,15 +61,42 @@ def c3():
     return box_graph_deleted(192, 128, 96, 0.10, 20260, "vertex")
 
 
-def test_c3_fiedler_inverse_mixed_vs_oracle_checks(c3):
+C3_GOLD = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "c3_levels01.json")))
+
+
+@pytest.mark.parametrize("prec", ["mixed", "fp64"])
+@pytest.mark.parametrize("policy", ["none", "resolve"])
+def test_c3_first_levels_vs_oracle(c3, prec, policy):
+    """C3 against the oracle's own results (tests/golden/c3_levels01.json, an
+    hour of FP64 inverse iteration on the host): lambda_2 of the first split
+    within 1e-6, the weighted cut of the 2- and 4-part partitions within 2 %,
+    sizes exact."""
+    gold = C3_GOLD
+    assert (c3.n, c3.nnz) == (gold["mesh"]["n"], gold["mesh"]["nnz"])
+    G = R.graph(c3)
+    o = R.options(method="inverse", precision=prec, degenerate_policy=policy, polish_cycles=8)
+    p2, st2, code2 = R.rsb_partition(G, 2, o)
+    assert code2 == 0
+    lam0 = gold["splits"][0]["lambda2"]
+    assert abs(st2["lambda_first"] - lam0) <= 1e-6 * lam0, (st2["lambda_first"], lam0)
+    cut2 = O.weighted_cut(c3, p2.cpu().numpy() == 0)
+    assert abs(cut2 - gold["weighted_cut_2"]) <= 0.02 * gold["weighted_cut_2"]
+    p4, st4, code4 = R.rsb_partition(G, 4, o)
+    assert code4 == 0
+    p4 = p4.cpu().numpy()
+    assert _sizes_ok(p4, c3.n, 4)
+    cut4 = O.partition_metrics(c3, p4, 4)["weighted_cut"]
+    assert abs(cut4 - gold["weighted_cut_4"]) <= 0.02 * gold["weighted_cut_4"], (cut4,)
+
+
+def test_c3_fiedler_vs_oracle(c3):
     G = R.graph(c3)
     lam, v, res, code = R.rsb_fiedler(G, R.options(method="inverse", precision="mixed",
                                                    degenerate_policy="none", polish_cycles=8))
-    assert code in (0, R.rsb.RSB_ENOCONV)
+    assert code == 0
+    lam0 = C3_GOLD["splits"][0]["lambda2"]
+    assert abs(lam - lam0) <= 1e-6 * lam0
     _check_fiedler_with_oracle(c3, lam, v.cpu().numpy())
-    lam64, v64, res64, _ = R.rsb_fiedler(G, R.options(method="inverse", precision="fp64"))
-    assert abs(lam64 - lam) <= 1e-6 * lam64
-    _check_fiedler_with_oracle(c3, lam64, v64.cpu().numpy(), rel=1e-8)
 
 
 def test_c3_partition_inverse_mixed(c3):
@@ -120,9 +155,10 @@ def test_c4_batch_equals_separate_calls(c4):
 
 
 def test_c5_partition_mixed_lanczos():
+    """The options bench.py times on this workload."""
     g = box_graph_deleted(256, 256, 256, 0.05, 20261, "vertex")
     G = R.graph(g)
-    opts = R.options(precision="mixed", degenerate_policy="none", polish_cycles=8)
+    opts = R.options(precision="mixed", degenerate_policy="none")
     lam, v, res, code = R.rsb_fiedler(G, opts)
     _check_fiedler_with_oracle(g, lam, v.cpu().numpy())
     part, st, code = R.rsb_partition(G, 1024, opts)
@@ -130,3 +166,6 @@ def test_c5_partition_mixed_lanczos():
     assert _sizes_ok(part, g.n, 1024)
     assert st["levels"] == 10
     assert abs(st["lambda_first"] - lam) <= 1e-6 * lam
+    assert st["resid_max"] <= 1e-5
+    m = O.partition_metrics(g, part, 1024)
+    assert m["max_neighbours"] <= 40

@@ -118,6 +118,41 @@ def test_fig2_worked_example():
     assert abs(li - 4.0) < 1e-10
 
 
+def test_gather_scatter_fig2():
+    """§5 with the paper's Fig. 2 vertex lists: A_w = P^T Q Q^T P gives the
+    printed Laplacian, and x = e_1 reaches element 2 along two paths."""
+    vl, L, kv = _read_fig2()
+    ev = np.array(vl)
+    z = O.gs_adjacency_apply(ev, np.array([1.0, 0.0, 0.0]))
+    assert z[1] == kv["z2_for_x1"][0]
+    assert z[0] == 4.0                      # an element meets itself at its 4 vertices
+    Lgs = np.stack([O.gs_laplacian_apply(ev, e) for e in np.eye(3)], axis=1)
+    assert np.array_equal(Lgs, L)
+    assert np.array_equal(O.laplacian_dense(O.dual_graph_from_vertices(ev)), L)
+
+
+@pytest.mark.parametrize("g", [box_graph(5, 4, 3, "vertex"),
+                               box_graph_deleted(9, 7, 6, 0.1, 4, "vertex")])
+def test_gather_scatter_equals_assembled_dual_graph(g):
+    """The dual graph built from the hexes' vertex ids is the vertex-adjacency
+    graph of the generator, entry for entry, and the matrix-free action equals
+    the assembled one (exactly, for integer vectors)."""
+    ev = g.hex_vertices()
+    h = O.dual_graph_from_vertices(ev)
+    assert np.array_equal(h.row_ptr, g.row_ptr)
+    assert np.array_equal(h.col, g.col) and np.array_equal(h.w, g.w)
+    x = np.random.default_rng(1).integers(-5, 6, g.n).astype(np.float64)
+    assert np.array_equal(O.gs_laplacian_apply(ev, x), O.laplacian_apply(g, x))
+
+
+def test_planted_gather_scatter_mistake_is_caught():
+    """Forgetting the diagonal correction (L = A_w instead of D_w - A_w) fails L 1 = 0."""
+    vl, L, kv = _read_fig2()
+    ev = np.array(vl)
+    assert np.abs(O.gs_laplacian_apply(ev, np.ones(3))).max() == 0.0
+    assert np.abs(O.gs_adjacency_apply(ev, np.ones(3))).max() > 0.0
+
+
 # ---------------------------------------------------------------- dense eigensolver
 
 
@@ -224,6 +259,48 @@ def test_planted_solver_mistake_is_caught(monkeypatch):
     monkeypatch.setattr(M, "_fixed_basis", no_ones)
     bad = O.lanczos_fiedler(g, O.Options(max_restarts=3)).lam
     assert abs(bad - O.box_lambda2(9, 5, 3)) > 1e-3
+
+
+@pytest.mark.parametrize("dims", [(16, 8, 4), (16, 16, 8), (12, 12, 12), (20, 9, 7)])
+@pytest.mark.parametrize("b", [2, 3, 4])
+def test_block_lanczos_box_closed_form(dims, b):
+    """Block Lanczos (§9's block extension) reaches lambda_2 = 2 (1 - cos(pi / n_max))
+    also where two or three axes are equally long (lambda_2 repeated)."""
+    g = box_graph(*dims)
+    r = O.block_lanczos_fiedler(g, O.Options(block=b))
+    assert r.converged
+    assert abs(r.lam - O.box_lambda2(*dims)) < 1e-11
+    assert np.linalg.norm(O.laplacian_apply(g, r.v) - r.lam * r.v) <= 1e-10 * O.degree(g).max()
+
+
+@pytest.mark.parametrize("seed", [11, 12])
+def test_block_lanczos_random_graph_vs_jacobi(seed):
+    g = random_graph(150, 300, seed)
+    lam = O.jacobi_eigh(O.laplacian_dense(g))[0][1]
+    for b in (2, 3):
+        r = O.block_lanczos_fiedler(g, O.Options(block=b))
+        assert r.converged and abs(r.lam - lam) < 1e-10 * max(1.0, lam)
+
+
+def test_block_lanczos_agrees_with_single_vector_on_deleted_mesh():
+    g = box_graph_deleted(14, 11, 9, 0.1, 7, "vertex")
+    one = O.lanczos_fiedler(g, O.Options())
+    for b in (2, 3, 4):
+        r = O.block_lanczos_fiedler(g, O.Options(block=b))
+        assert abs(r.lam - one.lam) < 1e-11 * one.lam
+        assert min(np.abs(r.v - one.v).max(), np.abs(r.v + one.v).max()) < 1e-6
+
+
+def test_planted_block_normalisation_mistake_is_caught(monkeypatch):
+    """Using the residual block without its Cholesky normalisation leaves S in a
+    non-orthonormal basis: the Ritz value misses the closed form."""
+    import oracle.rsb_oracle as M
+
+    g = box_graph(16, 8, 4)
+    monkeypatch.setattr(M, "_chol_scaled", lambda G, tiny, pmin: np.eye(G.shape[0]))
+    with np.errstate(all="ignore"):
+        r = O.block_lanczos_fiedler(g, O.Options(block=3, max_restarts=3))
+    assert not np.isfinite(r.lam) or abs(r.lam - O.box_lambda2(16, 8, 4)) > 1e-6
 
 
 # ---------------------------------------------------------------- split rules
@@ -337,6 +414,45 @@ def test_planted_neighbour_count_mistake_is_caught(monkeypatch):
     i, j = np.arange(16) % 4, np.arange(16) // 4
     quad = ((i >= 2) + 2 * (j >= 2)).astype(np.int32)
     assert per_edge(g, quad, 4)["max_neighbours"] != 2
+
+
+def test_rcb_box_hand_derived():
+    """RCB of the 16x8x4 box into 8 parts, derived by hand: x (extent 15), then
+    x again (8x8x4: equal extents 7, lowest axis), then y (4x8x4)."""
+    g = box_graph(16, 8, 4)
+    i, j = np.arange(512) % 16, (np.arange(512) // 16) % 8
+    expect = 4 * (i >= 8) + 2 * ((i % 8) >= 4) + (j >= 4)
+    assert np.array_equal(O.rcb_partition(g.centroids(), g.gid, 8), expect)
+
+
+def test_rcb_bruteforce_and_sizes():
+    rng = np.random.default_rng(3)
+    for trial in range(20):
+        n = int(rng.integers(2, 15))
+        pts = rng.random((n, 3))
+        gid = rng.permutation(1000)[:n].astype(np.int64)
+        part = O.rcb_partition(pts, gid, 2, tie_rel=0.0)
+        ax = int(np.argmax(pts.max(0) - pts.min(0)))
+        k = n // 2
+        order = np.lexsort((gid, pts[:, ax]))
+        assert set(np.nonzero(part == 0)[0]) == set(order[:k].tolist())
+    for P in (3, 5, 7):
+        g = box_graph_deleted(9, 7, 5, 0.1, 2)
+        part = O.rcb_partition(g.centroids(), g.gid, P)
+        assert np.array_equal(np.bincount(part, minlength=P),
+                              [O.seg_size(p, p + 1, g.n, P) for p in range(P)])
+
+
+def test_rsb_does_not_depend_on_row_order():
+    """RSB is defined through gids (start vectors, ties, orientation): a graph
+    with its rows permuted gives the same part for every element."""
+    from meshgen import permute_graph
+
+    for g in (box_graph(12, 6, 5), box_graph_deleted(10, 8, 6, 0.1, 4, "vertex")):
+        h = permute_graph(g, 9)
+        a = O.rsb_partition(g, 4, O.Options(degenerate="none"))
+        b = O.rsb_partition(h, 4, O.Options(degenerate="none"))
+        assert np.array_equal(a[h.meta["perm"]], b)
 
 
 # ---------------------------------------------------------------- whole recursion
