@@ -124,6 +124,10 @@ typedef struct rsb_options {
                             on one GPU it makes the Laplacian's gathers local);
                             part ids are still returned in caller order; needs
                             coords.  0: keep the caller's order                    */
+  int amg;               /* RSB_INVERSE: 1 solves L x = b by flexible CG
+                            preconditioned with an aggregation AMG V-cycle (§7,
+                            Algorithm 3; pairs of consecutive rows, RCB order with
+                            reorder = 1); 0 plain CG                               */
 } rsb_options;
 
 typedef struct rsb_stats {
@@ -143,7 +147,7 @@ typedef struct rsb_stats {
  * tol 1e-10, cg_tol 1e-12, cg_maxit 4000, max_outer 50, RESOLVE,
  * cluster_tol 0.05, tie_rel 1e-5, mixed_tol 1e-6, batched 1, use_graph 3,
  * validate 0, polish_cycles 2, keep 8, tile_rows 0, polish_dim 16, block 1,
- * reorder 0. */
+ * reorder 0, amg 0. */
 void rsb_options_default(rsb_options *o);
 
 /*

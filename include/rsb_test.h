@@ -27,6 +27,7 @@ extern "C" {
  *   5 Laplacian action of rsb_laplacian_bench
  *   6 the persistent Lanczos kernels (bytes of all of their phases)
  *   7 FP32 step A's first Gram-Schmidt dots, k_lz_a2
+ *   8 the AMG V-cycles of the flexible CG (time only)
  * Bytes count 4 B per stored SELL entry (padding included), every vector
  * element read or written once, and FP64 deflation vectors.  The event
  * records add a few microseconds per launch, so profiled calls run slower.

@@ -16,7 +16,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 OUT_DIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT_DIR, "librsb.so")
-SOURCES = ["graph.cu", "select.cu", "solver.cu", "block.cu", "gs.cu", "api.cu", "noalloc.cu"]
+SOURCES = ["graph.cu", "select.cu", "solver.cu", "block.cu", "gs.cu", "amg.cu", "api.cu", "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

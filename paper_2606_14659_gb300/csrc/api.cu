@@ -61,7 +61,8 @@ int solver_lanczos(const LevelGraph& G, const Tile* tiles, int ntiles, Unit* uni
 int solver_inverse(const LevelGraph& G, const Tile* tiles, int ntiles, Unit* units, int nunits,
                    const uint64_t* ckey, SolveBufs& B, int f32, uint64_t sd, const double* from64,
                    const float* from32, double cg_tol, int cg_maxit, int max_outer, int use_graph,
-                   cudaStream_t s);
+                   cudaStream_t s, const std::vector<Unit>* amg_units);
+void amg_release();
 int solver_write_vector(const LevelGraph& G, const Tile* tiles, int ntiles, Unit* units,
                         const uint64_t* ckey, SolveBufs& B, int f32, int from_x, double* out,
                         int cand, int better_only, cudaStream_t s);
@@ -71,6 +72,7 @@ int solver_quartic(const Tile* tiles, int ntiles, Unit* units, int nunits, const
                    cudaStream_t s);
 int solver_cluster_check(Unit* units, int nunits, int nd, double cluster_tol, cudaStream_t s);
 int solver_stats(const Unit* units, int nunits, int* capped, double* resid_max, cudaStream_t s);
+int solver_sum_inner(const Unit* units, int nunits, long long* inner, cudaStream_t s);
 int solver_rq_refine(const LevelGraph& G, const Tile* tiles, int ntiles, Unit* units, int nunits,
                      const uint64_t* ckey, SolveBufs& B, const float* from32, cudaStream_t s);
 
@@ -320,6 +322,7 @@ struct Counters {
   double resid_max;
   GridBar gb;
   int jmin[2];
+  long long inner;  // CG iterations of the inverse-iteration solves
 };
 
 // ----------------------------------------------------------------------------
@@ -384,12 +387,14 @@ extern "C" void rsb_options_default(rsb_options* o) {
   o->polish_dim = 16;
   o->block = 1;
   o->reorder = 0;
+  o->amg = 0;
 }
 
 static int check_options(const rsb_options& o) {
   if (o.method != RSB_LANCZOS && o.method != RSB_INVERSE && o.method != RSB_RCB)
     return rsb_set_error(RSB_EINVAL, "method");
   if (o.reorder != 0 && o.reorder != 1) return rsb_set_error(RSB_EINVAL, "reorder");
+  if (o.amg != 0 && o.amg != 1) return rsb_set_error(RSB_EINVAL, "amg");
   if (o.precision != RSB_FP64 && o.precision != RSB_MIXED)
     return rsb_set_error(RSB_EINVAL, "precision");
   if (o.krylov_dim < 1 || o.krylov_dim > RSB_MAXM) return rsb_set_error(RSB_EINVAL, "krylov_dim");
@@ -594,7 +599,7 @@ struct RunStats {
 
 static int solve_candidate(Ctx& c, const LevelGraph& G, const Tile* tiles, int ntiles, Unit* units,
                            int nunits, int64_t maxn, const rsb_options& o, int cand,
-                           RunStats& rs) {
+                           RunStats& rs, const std::vector<Unit>& hunits) {
   const int nd = cand;
   const int64_t dim = maxn - 1 - nd;
   if (dim <= 0) return RSB_OK;
@@ -649,7 +654,11 @@ static int solve_candidate(Ctx& c, const LevelGraph& G, const Tile* tiles, int n
   if (inverse) {
     const double cgt = mixed ? std::max(o.cg_tol, 1e-6) : o.cg_tol;
     rc = solver_inverse(G, tiles, ntiles, units, nunits, ckey, B, mixed, sd, nullptr, nullptr, cgt,
-                        o.cg_maxit, o.max_outer, use_graph, c.s);
+                        o.cg_maxit, o.max_outer, use_graph, c.s, o.amg ? &hunits : nullptr);
+    if (!rc) {
+      RSB_CK(cudaMemsetAsync(&cn->inner, 0, sizeof(long long), c.s));
+      rc = solver_sum_inner(units, nunits, &cn->inner, c.s);
+    }
   } else {
     rc = solver_lanczos(G, tiles, ntiles, units, nunits, ckey, B, mixed, M, sd, nullptr, nullptr,
                         use_graph, c.s);
@@ -706,6 +715,7 @@ static int solve_candidate(Ctx& c, const LevelGraph& G, const Tile* tiles, int n
             (long long)h.cycles, h.capped, h.resid_max);
   rs.solves += 1;
   rs.cycles += h.cycles;
+  if (inverse) rs.inner += h.inner;
   rs.nonconv += h.capped;
   rs.resid_max = std::max(rs.resid_max, h.resid_max);
   return RSB_OK;
@@ -755,7 +765,8 @@ static int split_units(Ctx& c, const LevelGraph& G, std::vector<Unit>& hunits,
   if ((rc = launch_degree_max(G, tiles, ntiles, units, ckey, partials, c.s))) return rc;
   const int ncmax = o.degenerate_policy == RSB_DEGEN_RESOLVE ? 3 : 1;
   for (int cand = 0; cand < ncmax; ++cand) {
-    if ((rc = solve_candidate(c, G, tiles, ntiles, units, nunits, maxn, o, cand, rs))) return rc;
+    if ((rc = solve_candidate(c, G, tiles, ntiles, units, nunits, maxn, o, cand, rs, hunits)))
+      return rc;
     if (cand > 0 && (rc = solver_cluster_check(units, nunits, cand, o.cluster_tol, c.s))) return rc;
   }
   double* v0 = dptr<double>(c.cand[0]);
@@ -1431,7 +1442,7 @@ extern "C" int rsb_fiedler(const rsb_csr* g, const rsb_options* opt, double* lam
   if ((rc = launch_degree_max(G, tiles, ntiles, units, dptr<uint64_t>(c.ckey), partials, c.s)))
     return end_call(c, stream, rc);
   RunStats rs;
-  if ((rc = solve_candidate(c, G, tiles, ntiles, units, 1, N, o, 0, rs)))
+  if ((rc = solve_candidate(c, G, tiles, ntiles, units, 1, N, o, 0, rs, hunits)))
     return end_call(c, stream, rc);
   if ((rc = launch_orient(G, tiles, ntiles, units, dptr<uint64_t>(c.ckey), dptr<double>(c.cand[0]),
                           0, o.tie_rel, partials, c.s)))
@@ -1755,6 +1766,7 @@ extern "C" const char* rsb_strerror(int code) {
 extern "C" const char* rsb_last_error_detail(void) { return g_detail.c_str(); }
 
 extern "C" void rsb_release(void) {
+  amg_release();
   for (int d = 0; d < 64; ++d) {
     Ctx* c = g_ctx[d];
     if (!c) continue;

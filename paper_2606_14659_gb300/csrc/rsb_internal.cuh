@@ -91,6 +91,8 @@ struct Unit {
   double cp[1 + RSB_MAXD];
   // CG scalars (§7): FP64 recurrences in both precisions
   double rr, cg_alpha, cg_beta, bnorm;
+  double fz_rz, fz_ro;          // flexible CG: z.r and z.r_old of the new z
+  double cz[1 + RSB_MAXD];      // flexible CG: projection coefficients of z
   double rq, lnorm2;
   // select / split
   double vmax, vmin, amax;
@@ -505,7 +507,7 @@ void rsb_count_launch(int k = 1);
 // Kernel timing (rsb_profile_begin/end): families of include/rsb.h.
 enum {
   PROF_NONE = 0, PROF_LZ_A = 1, PROF_LZ_B = 2, PROF_LZ_C = 3, PROF_CG_AP = 4, PROF_SPMV = 5,
-  PROF_CYCLE = 6, PROF_LZ_A2 = 7, PROF_NFAM = 8
+  PROF_CYCLE = 6, PROF_LZ_A2 = 7, PROF_AMG = 8, PROF_NFAM = 9
 };
 int prof_before(int family, cudaStream_t s);      // event pair index or -1
 void prof_after(int idx, cudaStream_t s);

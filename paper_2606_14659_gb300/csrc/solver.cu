@@ -465,7 +465,7 @@ __global__ void __launch_bounds__(RSB_BLOCK, 2) k_lz_bt(LzArgs<V> a, int j, Grid
   const Tile t = a.tiles[blockIdx.x];
   Unit& u = a.units[t.unit];
   if (u.status != U_ACTIVE || j >= u.msteps || j < u.j0) return;
-  V* Qb = reinterpret_cast<V*>(bt_sh);  // [2][nq][CRB]
+  V* Qb = reinterpret_cast<V*>(bt_sh);  // [2][nq + 1][CRB]: q_0..q_j, then w
   const int nd = u.nd;
   const int nc = 2 + nd + j;
   const int nq = j + 1;
@@ -477,23 +477,27 @@ __global__ void __launch_bounds__(RSB_BLOCK, 2) k_lz_bt(LzArgs<V> a, int j, Grid
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   stage_coef<V, false>(u.c1, nc, u.isn, cv);  // ends with a CTA barrier
-  if (threadIdx.x == 0) bulk_issue_chunk(a, Qb, bar, nq, 0, t.row0, min(t.row1, t.row0 + RSB_BLOCK));
+  // w is staged with the basis (its rows of a chunk are rewritten only after
+  // that chunk's copies landed; rows the 16-byte rounding adds are not used)
+  if (threadIdx.x == 0)
+    bulk_issue_chunk(a, Qb, bar, nq, 0, t.row0, min(t.row1, t.row0 + RSB_BLOCK), (const V*)w_);
   Acc<V> acc[MAXCW];
   unsigned long long pbytes = 0;
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   for (int ci = 0; ci < nchunk; ++ci) {
     if (threadIdx.x == 0 && ci + 1 < nchunk) {
       const int n0 = t.row0 + (ci + 1) * RSB_BLOCK;
-      bulk_issue_chunk(a, Qb, bar, nq, (ci + 1) & 1, n0, min(t.row1, n0 + RSB_BLOCK));
+      bulk_issue_chunk(a, Qb, bar, nq, (ci + 1) & 1, n0, min(t.row1, n0 + RSB_BLOCK),
+                       (const V*)w_);
     }
     if (!bulk_wait_chunk(bar, ci, nchunk, gb)) return;
     const int c0 = t.row0 + ci * RSB_BLOCK;
     const int c1 = min(t.row1, c0 + RSB_BLOCK);
-    const V* Qc = Qb + (size_t)(ci & 1) * nq * CRB + (c0 - (c0 & ~(AL - 1)));
+    const V* Qc = Qb + (size_t)(ci & 1) * (nq + 1) * CRB + (c0 - (c0 & ~(AL - 1)));
     const int r = c0 + threadIdx.x;
     V wv = V(0);
     if (r < c1) {
-      wv = w_[r];
+      wv = Qc[(size_t)nq * CRB + threadIdx.x];
       if (unit_has(u, a.ckey, r)) wv -= cv[0];
       for (int l = 0; l < nd; ++l) wv -= cv[1 + l] * V((l == 0 ? a.D0 : a.D1)[r]);
       const V* cq = cv + 1 + nd;
@@ -1541,7 +1545,7 @@ static int lz_cycle(LzArgs<V>& a, int ntiles, int nunits, int M, double breakdow
     prof_after(pi, s);
     pi = prof_before(PROF_LZ_B, s);
     if (sizeof(V) == 4) {  // FP32: bandwidth-bound, basis staged by bulk copies
-      k_lz_bt<V><<<ntiles, RSB_BLOCK, lz_bt_smem<V>(j + 1), s>>>(a, j, gb);
+      k_lz_bt<V><<<ntiles, RSB_BLOCK, lz_bt_smem<V>(j + 2), s>>>(a, j, gb);
       RSB_CKL("k_lz_bt");
     } else {  // FP64: bound by GB300's FP64 rate; the register-streaming kernel is faster
       k_lz_b<V><<<ntiles, RSB_BLOCK, 0, s>>>(a, j);
@@ -1645,11 +1649,11 @@ static int lanczos_run(const LevelGraph& G, const Tile* tiles, int ntiles, Unit*
     }
     return rc;
   }
-  // the staged step B (FP32) needs up to 2 * M * (RSB_BLOCK + 4) floats of
-  // dynamic shared memory (83 KB at M = 40)
+  // the staged step B (FP32) needs up to 2 * (M + 1) * (RSB_BLOCK + 4) floats of
+  // dynamic shared memory (85 KB at M = 40)
   if (sizeof(V) == 4) {
     RSB_CK(cudaFuncSetAttribute(k_lz_bt<V>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)lz_bt_smem<V>(M)));
+                                (int)lz_bt_smem<V>(M + 1)));
     RSB_CK(cudaFuncSetAttribute(k_lz_a2<V>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)lz_bt_smem<V>(M + 1)));
   }
@@ -1832,6 +1836,146 @@ __global__ void __launch_bounds__(RSB_BLOCK) k_cg_p(LzArgs<V> a) {
   }
 }
 
+// ----------------------------------------------------------------------------
+// Flexible CG (§7): the first direction is the residual itself, later ones the
+// AMG-preconditioned residual z; beta = z.(r - r_old) / (z_old . r_old).  With
+// u.rr holding z.r, k_cg_ap gives alpha = z.r / p.Ap as in plain CG.
+// ----------------------------------------------------------------------------
+// x += alpha p; r_old = r (in W1); r -= alpha Ap; sums for ||r||^2 and the
+// projection of r; convergence as in plain CG.
+template <typename V>
+__global__ void __launch_bounds__(RSB_BLOCK) k_fcg_xr(LzArgs<V> a, double cg_tol, int cg_maxit,
+                                                      int* n_cg) {
+  __shared__ double sm[RSB_WARPS];
+  __shared__ double out[2 + RSB_MAXD];
+  const Tile t = a.tiles[blockIdx.x];
+  Unit& u = a.units[t.unit];
+  if (u.status != U_ACTIVE || u.cg_done) return;
+  const int nd = u.nd;
+  const V al = V(u.cg_alpha);
+  Acc<V> r2, rs, d0, d1;
+  for (int r = t.row0 + threadIdx.x; r < t.row1; r += RSB_BLOCK) {
+    a.X[r] += al * a.P[r];
+    const V ro = a.R[r];
+    const V rr = ro - al * a.AP[r];
+    a.W1[r] = ro;
+    a.R[r] = rr;
+    r2.add(rr * rr);
+    rs.add(rr);
+    if (nd > 0) d0.add(V(a.D0[r]) * rr);
+    if (nd > 1) d1.add(V(a.D1[r]) * rr);
+  }
+  double v[4] = {r2.get(), rs.get(), d0.get(), d1.get()};
+  const int nv = 2 + nd;
+  for (int c = 0; c < nv; ++c) {
+    const double sum = block_sum(v[c], sm);
+    if (threadIdx.x == 0) a.partials[(long long)c * a.stride + blockIdx.x] = sum;
+  }
+  if (last_cta(&u.cnt, u.ntile)) {
+    final_reduce(a.partials, a.stride, u.tile0, u.ntile, nv, out);
+    if (threadIdx.x == 0) {
+      double cp2 = 0.0;
+      u.cp[0] = out[1] * u.isn;
+      cp2 += u.cp[0] * u.cp[0];
+      for (int l = 0; l < nd; ++l) {
+        u.cp[1 + l] = out[2 + l];
+        cp2 += u.cp[1 + l] * u.cp[1 + l];
+      }
+      const double rrn = fmax(out[0] - cp2, 0.0);
+      u.inner += 1;
+      u.inner_total += 1;
+      if (sqrt(rrn) <= cg_tol * u.bnorm || u.inner >= cg_maxit) {
+        u.cg_done = 1;
+        atomicSub(n_cg, 1);
+      }
+    }
+  }
+}
+
+// r -= B cp (projection): the residual the preconditioner sees
+template <typename V>
+__global__ void __launch_bounds__(RSB_BLOCK) k_fcg_proj(LzArgs<V> a) {
+  const Tile t = a.tiles[blockIdx.x];
+  const Unit& u = a.units[t.unit];
+  if (u.status != U_ACTIVE || u.cg_done) return;
+  const int nd = u.nd;
+  for (int r = t.row0 + threadIdx.x; r < t.row1; r += RSB_BLOCK) {
+    V v = a.R[r];
+    if (unit_has(u, a.ckey, r)) v -= V(u.cp[0] * u.isn);
+    if (nd > 0) v -= V(u.cp[1]) * V(a.D0[r]);
+    if (nd > 1) v -= V(u.cp[2]) * V(a.D1[r]);
+    a.R[r] = v;
+  }
+}
+
+// z (in Y) restricted to the unit's rows; z.r, z.r_old and the projection sums of z
+template <typename V>
+__global__ void __launch_bounds__(RSB_BLOCK) k_fcg_z(LzArgs<V> a) {
+  __shared__ double sm[RSB_WARPS];
+  __shared__ double out[3 + RSB_MAXD];
+  const Tile t = a.tiles[blockIdx.x];
+  Unit& u = a.units[t.unit];
+  if (u.status != U_ACTIVE || u.cg_done) return;
+  const int nd = u.nd;
+  Acc<V> zr, zo, zs, d0, d1;
+  for (int r = t.row0 + threadIdx.x; r < t.row1; r += RSB_BLOCK) {
+    V z = a.Y[r];
+    if (!unit_has(u, a.ckey, r)) {
+      z = V(0);
+      a.Y[r] = z;
+    }
+    zr.add(z * a.R[r]);
+    zo.add(z * a.W1[r]);
+    zs.add(z);
+    if (nd > 0) d0.add(V(a.D0[r]) * z);
+    if (nd > 1) d1.add(V(a.D1[r]) * z);
+  }
+  double v[5] = {zr.get(), zo.get(), zs.get(), d0.get(), d1.get()};
+  const int nv = 3 + nd;
+  for (int c = 0; c < nv; ++c) {
+    const double sum = block_sum(v[c], sm);
+    if (threadIdx.x == 0) a.partials[(long long)c * a.stride + blockIdx.x] = sum;
+  }
+  if (last_cta(&u.cnt, u.ntile)) {
+    final_reduce(a.partials, a.stride, u.tile0, u.ntile, nv, out);
+    if (threadIdx.x == 0) {
+      u.fz_rz = out[0];
+      u.fz_ro = out[1];
+      u.cz[0] = out[2] * u.isn;
+      for (int l = 0; l < nd; ++l) u.cz[1 + l] = out[3 + l];
+    }
+  }
+}
+
+// z -= B cz; p = z + beta p with the flexible beta; z.r becomes the new rr
+template <typename V>
+__global__ void __launch_bounds__(RSB_BLOCK) k_fcg_p(LzArgs<V> a) {
+  const Tile t = a.tiles[blockIdx.x];
+  Unit& u = a.units[t.unit];
+  if (u.status != U_ACTIVE || u.cg_done) return;
+  const int nd = u.nd;
+  const double rz = u.fz_rz;
+  const V be = V((rz - u.fz_ro) / u.rr);
+  for (int r = t.row0 + threadIdx.x; r < t.row1; r += RSB_BLOCK) {
+    V z = a.Y[r];
+    if (unit_has(u, a.ckey, r)) z -= V(u.cz[0] * u.isn);
+    if (nd > 0) z -= V(u.cz[1]) * V(a.D0[r]);
+    if (nd > 1) z -= V(u.cz[2]) * V(a.D1[r]);
+    a.P[r] = z + be * a.P[r];
+  }
+  // every CTA of the unit has read u.rr above; the unit's rr is rewritten by
+  // the next launch that needs it (k_fcg_rr), after this kernel has finished
+}
+
+template <typename V>
+__global__ void k_fcg_rr(Unit* units, int nunits) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nunits) return;
+  Unit& u = units[i];
+  if (u.status != U_ACTIVE || u.cg_done) return;
+  u.rr = u.fz_rz;
+}
+
 // Outer step: y = x; Ly, yLy, yy -> Rayleigh quotient.
 template <typename V>
 __global__ void __launch_bounds__(RSB_BLOCK) k_inv_rq(LzArgs<V> a) {
@@ -1917,18 +2061,41 @@ __global__ void k_count_cg(Unit* units, int nunits, int* n_cg) {
   if (i < nunits && units[i].status == U_ACTIVE && !units[i].cg_done) atomicAdd(n_cg, 1);
 }
 
+int amg_setup(int f32, const LevelGraph& G, const Tile* tiles, int ntiles, const Unit* units,
+              const std::vector<Unit>& hunits, cudaStream_t s);
+int amg_apply(int f32, const LevelGraph& G, const Tile* tiles, int ntiles, const Unit* units,
+              const void* r, void* z, cudaStream_t s);
+
 template <typename V>
 static int cg_block(LzArgs<V>& a, int ntiles, int iters, double cg_tol, int cg_maxit, int* n_cg,
-                    cudaStream_t s) {
+                    cudaStream_t s, const LevelGraph* amgG = nullptr, int nunits = 0) {
   for (int i = 0; i < iters; ++i) {
     const int pi = prof_before(PROF_CG_AP, s);
     k_cg_ap<V><<<ntiles, RSB_BLOCK, 0, s>>>(a);
     RSB_CKL("k_cg_ap");
     prof_after(pi, s);
-    k_cg_xr<V><<<ntiles, RSB_BLOCK, 0, s>>>(a, cg_tol, cg_maxit, n_cg);
-    RSB_CKL("k_cg_xr");
-    k_cg_p<V><<<ntiles, RSB_BLOCK, 0, s>>>(a);
-    RSB_CKL("k_cg_p");
+    if (!amgG) {
+      k_cg_xr<V><<<ntiles, RSB_BLOCK, 0, s>>>(a, cg_tol, cg_maxit, n_cg);
+      RSB_CKL("k_cg_xr");
+      k_cg_p<V><<<ntiles, RSB_BLOCK, 0, s>>>(a);
+      RSB_CKL("k_cg_p");
+      continue;
+    }
+    // flexible CG preconditioned by one AMG V-cycle (§7)
+    k_fcg_xr<V><<<ntiles, RSB_BLOCK, 0, s>>>(a, cg_tol, cg_maxit, n_cg);
+    RSB_CKL("k_fcg_xr");
+    k_fcg_proj<V><<<ntiles, RSB_BLOCK, 0, s>>>(a);
+    RSB_CKL("k_fcg_proj");
+    const int pv = prof_before(PROF_AMG, s);
+    int rc = amg_apply(sizeof(V) == 4, *amgG, a.tiles, ntiles, a.units, a.R, a.Y, s);
+    if (rc) return rc;
+    prof_after(pv, s);
+    k_fcg_z<V><<<ntiles, RSB_BLOCK, 0, s>>>(a);
+    RSB_CKL("k_fcg_z");
+    k_fcg_p<V><<<ntiles, RSB_BLOCK, 0, s>>>(a);
+    RSB_CKL("k_fcg_p");
+    k_fcg_rr<V><<<(nunits + 127) / 128, 128, 0, s>>>(a.units, nunits);
+    RSB_CKL("k_fcg_rr");
   }
   return RSB_OK;
 }
@@ -1937,13 +2104,19 @@ template <typename V>
 static int inverse_run(const LevelGraph& G, const Tile* tiles, int ntiles, Unit* units, int nunits,
                        const uint64_t* ckey, SolveBufs& B, uint64_t sd, const double* from64,
                        const float* from32, double cg_tol, int cg_maxit, int max_outer,
-                       int use_graph, int64_t* inner_out, cudaStream_t s) {
+                       int use_graph, int64_t* inner_out, cudaStream_t s,
+                       const std::vector<Unit>* amg_units) {
   LzArgs<V> a = make_args<V>(G, tiles, ntiles, units, ckey, B);
   int active = 0;
   int rc = read_active(B, s, &active);
   if (rc || active == 0) return rc;
   rc = lz_start<V>(a, ntiles, sd, from64, from32, s);  // W0 = projected start, beta0
   if (rc) return rc;
+  const LevelGraph* amgG = nullptr;
+  if (amg_units) {  // the hierarchy of every unit of the level (§7)
+    if ((rc = amg_setup(sizeof(V) == 4, G, tiles, ntiles, units, *amg_units, s))) return rc;
+    amgG = &G;
+  }
   const int CGK = 8;
   cudaGraphExec_t exec = nullptr;
   std::vector<int> cap_pairs;
@@ -1951,7 +2124,7 @@ static int inverse_run(const LevelGraph& G, const Tile* tiles, int ntiles, Unit*
     cudaGraph_t graph = nullptr;
     RSB_CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
     prof_capture_begin();
-    rc = cg_block<V>(a, ntiles, CGK, cg_tol, cg_maxit, B.n_cg, s);
+    rc = cg_block<V>(a, ntiles, CGK, cg_tol, cg_maxit, B.n_cg, s, amgG, nunits);
     cap_pairs = prof_capture_end();
     cudaError_t e = cudaStreamEndCapture(s, &graph);
     if (rc) {
@@ -1972,14 +2145,14 @@ static int inverse_run(const LevelGraph& G, const Tile* tiles, int ntiles, Unit*
     for (int blk = 0; blk < cg_maxit / CGK + 2; ++blk) {
       if (exec) {
         cudaError_t e = cudaGraphLaunch(exec, s);
-        rsb_count_launch(3 * CGK);
+        rsb_count_launch((amgG ? 7 + 13 * 20 : 3) * CGK);
         if (e != cudaSuccess) {
           cudaGraphExecDestroy(exec);
           return rsb_set_cuda_error(e, "cudaGraphLaunch");
         }
         prof_replay(cap_pairs);
       } else {
-        rc = cg_block<V>(a, ntiles, CGK, cg_tol, cg_maxit, B.n_cg, s);
+        rc = cg_block<V>(a, ntiles, CGK, cg_tol, cg_maxit, B.n_cg, s, amgG, nunits);
         if (rc) break;
       }
       int ncg = 0;
@@ -2010,13 +2183,13 @@ static int inverse_run(const LevelGraph& G, const Tile* tiles, int ntiles, Unit*
 int solver_inverse(const LevelGraph& G, const Tile* tiles, int ntiles, Unit* units, int nunits,
                    const uint64_t* ckey, SolveBufs& B, int f32, uint64_t sd, const double* from64,
                    const float* from32, double cg_tol, int cg_maxit, int max_outer, int use_graph,
-                   cudaStream_t s) {
+                   cudaStream_t s, const std::vector<Unit>* amg_units) {
   if (ntiles <= 0 || nunits <= 0) return RSB_OK;
   if (f32)
     return inverse_run<float>(G, tiles, ntiles, units, nunits, ckey, B, sd, from64, from32, cg_tol,
-                              cg_maxit, max_outer, use_graph, nullptr, s);
+                              cg_maxit, max_outer, use_graph, nullptr, s, amg_units);
   return inverse_run<double>(G, tiles, ntiles, units, nunits, ckey, B, sd, from64, from32, cg_tol,
-                             cg_maxit, max_outer, use_graph, nullptr, s);
+                             cg_maxit, max_outer, use_graph, nullptr, s, amg_units);
 }
 
 // ----------------------------------------------------------------------------
@@ -2285,6 +2458,21 @@ __global__ void k_solve_stats(const Unit* units, int nunits, int* capped, double
     atomicMax((unsigned long long*)resid_max, (unsigned long long)__double_as_longlong(r));
   }
   (void)cand;
+}
+
+// CG iterations of the inverse-iteration solve just finished, summed over units
+__global__ void k_sum_inner(const Unit* units, int nunits, long long* inner) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nunits) return;
+  const Unit& u = units[i];
+  if (u.status == U_CONVERGED || u.status == U_CAPPED)
+    atomicAdd((unsigned long long*)inner, (unsigned long long)u.inner_total);
+}
+
+int solver_sum_inner(const Unit* units, int nunits, long long* inner, cudaStream_t s) {
+  k_sum_inner<<<(nunits + 127) / 128, 128, 0, s>>>(units, nunits, inner);
+  RSB_CKL("k_sum_inner");
+  return RSB_OK;
 }
 
 int solver_stats(const Unit* units, int nunits, int* capped, double* resid_max, cudaStream_t s) {

@@ -45,7 +45,7 @@ class rsb_options(C.Structure):
                 ("tie_rel", C.c_double), ("mixed_tol", C.c_double), ("batched", C.c_int),
                 ("use_graph", C.c_int), ("validate", C.c_int), ("polish_cycles", C.c_int),
                 ("keep", C.c_int), ("tile_rows", C.c_int), ("polish_dim", C.c_int),
-                ("block", C.c_int), ("reorder", C.c_int)]
+                ("block", C.c_int), ("reorder", C.c_int), ("amg", C.c_int)]
 
 
 class rsb_stats(C.Structure):
@@ -408,7 +408,7 @@ def rsb_release():
 
 
 PROFILE_FAMILIES = {"lz_a": 1, "lz_b": 2, "lz_c": 3, "cg_ap": 4, "spmv": 5, "cycle": 6,
-                    "lz_a2": 7, "all": -1}
+                    "lz_a2": 7, "amg": 8, "all": -1}
 
 
 def rsb_profile_begin(family: str | int):

@@ -49,6 +49,7 @@ def test_binding_struct_layout_and_strerror():
 
     lib = R.load()
     assert ctypes.sizeof(R.rsb_options) == 120 and R.rsb_options.block.offset == 108
+    assert R.rsb_options.amg.offset == 116
     assert R.rsb_options.reorder.offset == 112 and ctypes.sizeof(R.rsb_csr) == 48
     assert R.rsb_options.keep.offset == 96 and R.rsb_options.tile_rows.offset == 100
     assert R.rsb_options.polish_dim.offset == 104

@@ -303,6 +303,76 @@ def test_planted_block_normalisation_mistake_is_caught(monkeypatch):
     assert not np.isfinite(r.lam) or abs(r.lam - O.box_lambda2(16, 8, 4)) > 1e-6
 
 
+def test_amg_galerkin_levels_are_laplacians():
+    """J L J^T of a pair aggregation is again a Laplacian (§7): rows sum to zero,
+    symmetric, non-positive off the diagonal; the last level is 1 x 1 and zero."""
+    g = box_graph_deleted(11, 9, 7, 0.1, 5, "vertex")
+    levels = O.amg_hierarchy(O.laplacian_csr(g))
+    assert levels[-1][0].shape == (1, 1) and levels[-1][0].toarray()[0, 0] == 0.0
+    sizes = [L.shape[0] for L, _ in levels]
+    assert all(b == (a + 1) // 2 for a, b in zip(sizes, sizes[1:]))
+    for L, _ in levels:
+        A = L.toarray()
+        assert np.abs(A.sum(axis=1)).max() == 0.0
+        assert np.array_equal(A, A.T)
+        assert (A - np.diag(np.diag(A)) <= 0).all()
+
+
+def test_amg_vcycle_converges_as_stationary_iteration():
+    g = box_graph(12, 10, 8)
+    L = O.laplacian_csr(g)
+    levels = O.amg_hierarchy(L)
+    rng = np.random.default_rng(4)
+    b = rng.standard_normal(g.n)
+    b -= b.mean()
+    x = np.zeros(g.n)
+    res = [np.linalg.norm(b)]
+    for _ in range(40):
+        x = x + O.vcycle(levels, 0, b - L @ x)
+        x -= x.mean()
+        res.append(np.linalg.norm(b - L @ x))
+    assert res[-1] < 1e-2 * res[0]
+    assert all(r1 < r0 for r0, r1 in zip(res, res[1:]))
+    # the coarse corrections matter: damped Jacobi alone, with the 5 fine-level
+    # sweeps a V-cycle makes (1 + 2 before, 2 after), barely moves the smooth error
+    d = 2.0 / 3.0 / L.diagonal()
+    xj = np.zeros(g.n)
+    for _ in range(40 * 5):
+        xj = xj + d * (b - L @ xj)
+    assert np.linalg.norm(b - L @ xj) > 10 * res[-1]
+
+
+def test_amg_fcg_solves_like_cg_with_fewer_iterations():
+    g = box_graph(24, 16, 12)
+    B = np.ones((g.n, 1)) / np.sqrt(g.n)
+    b = O.start_vector(g.gid, 9)
+    b -= b.mean()
+    b /= np.linalg.norm(b)
+    opts = O.Options(cg_tol=1e-11)
+    x1, i1 = O.cg_solve(g, b, B, opts)
+    x2, i2 = O.fcg_solve(g, b, B, opts)
+    assert np.abs(x1 - x2).max() < 1e-8 * np.abs(x1).max()
+    assert i2 < i1 / 2
+    assert np.linalg.norm(O.laplacian_apply(g, x2) - b) < 1e-10
+
+
+def test_amg_fcg_first_direction_unpreconditioned():
+    """§7: with b an eigenvector of L the flexible CG returns after one iteration."""
+    g = box_graph(16, 8, 4)
+    lam, v, _ = O.fiedler_of_graph(g)
+    B = np.ones((g.n, 1)) / np.sqrt(g.n)
+    x, it = O.fcg_solve(g, v, B, O.Options(cg_tol=1e-9))
+    assert it == 1
+    assert np.abs(x - v / lam).max() < 1e-8 * np.abs(v / lam).max()
+
+
+@pytest.mark.parametrize("dims", [(16, 8, 4), (12, 7, 5)])
+def test_amg_inverse_box_closed_form(dims):
+    g = box_graph(*dims)
+    r = O.fiedler(g, O.Options(method="inverse", amg=True))
+    assert r.converged and abs(r.lam - O.box_lambda2(*dims)) < 1e-11
+
+
 # ---------------------------------------------------------------- split rules
 
 
