@@ -72,7 +72,7 @@ WORKLOADS = {
 DEFAULT_FORMS = {"c1": ["fp64", "fp64_plain", "spmv", "cpu"],
                  "c2": ["fp64", "fp64_plain", "spmv", "cpu"],
                  "c3": ["fp64", "spmv", "cpu"], "c4": ["fp64", "cpu"],
-                 "c5": ["fp64", "spmv", "cpu"]}
+                 "c5": ["fp64", "spmv", "cpu", "frows"]}
 # bounded samples for the CPU oracle: meshes of the same kind as the workload
 # (same generator, adjacency, weights and deletion fraction), small enough for
 # a few to a few tens of seconds of host time
@@ -506,6 +506,9 @@ def our_arm(args):
             sp["f32_frac"] = sp["f32_gbs"] / peak
             extra["spmv"] = sp
 
+    if rank == 0 and "frows" in forms:
+        extra["next_rows"] = next_rows(R, gs[0], dev, flush)
+
     peak, peak_kind = _peaks()
     roof = None
     if dom is not None:
@@ -566,6 +569,76 @@ def our_arm(args):
     if dist is not None:
         dist.destroy_process_group()
     return 0
+
+
+# ----------------------------------------------------------------------------
+# the rows beyond the headline path: gather-scatter Laplacian, RCB and the RCB
+# reordering, AMG-preconditioned inverse iteration, block Lanczos
+# ----------------------------------------------------------------------------
+def _timed(torch, fn, flush):
+    flush.zero_()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    out = fn()
+    e1.record()
+    e1.synchronize()
+    return e0.elapsed_time(e1), out
+
+
+def next_rows(R, g5, dev, flush):
+    import torch
+
+    from meshgen import box_graph_deleted, permute_graph
+
+    out = {}
+    peak, _ = _peaks()
+    # f4: matrix-free Laplacian from the hex vertex ids of the headline mesh
+    ev = torch.from_numpy(g5.hex_vertices()).to(dev)
+    gs = {}
+    for f32 in (True, False):
+        ms, by = R.rsb.rsb_laplacian_bench_gs(ev, f32, 10)
+        gs["f32_gbs" if f32 else "f64_gbs"] = by / (ms * 1e6)
+        gs["f32_ms" if f32 else "f64_ms"] = ms
+    gs["f32_frac"] = gs["f32_gbs"] / peak
+    t0 = time.perf_counter()
+    n, rp, col, w = R.rsb.rsb_dual_graph(ev)
+    torch.cuda.synchronize()
+    gs["dual_graph_build_s"] = time.perf_counter() - t0
+    gs["dual_graph_nnz"] = int(col.numel())
+    out["gather_scatter_c5"] = gs
+    del ev, rp, col, w
+    # f3: RCB of the headline mesh into 1024 parts
+    G5 = R.graph(g5, device=dev)
+    o = R.options(method="rcb")
+    R.rsb_partition(G5, 1024, o)
+    ms, (p, st, code) = _timed(torch, lambda: R.rsb_partition(G5, 1024, o), flush)
+    out["rcb_c5_1024"] = {"ms": ms, "elements_bisected_per_s": st["elements_bisected"] / (ms / 1e3)}
+    del G5
+    # f3 and f2, f1 on the 2.1M-element C3 mesh (first split)
+    g3 = box_graph_deleted(192, 128, 96, 0.10, 20260, "vertex")
+    h3 = permute_graph(g3, 1)
+    G3 = R.graph(g3, device=dev)
+    H3 = R.graph(h3, device=dev)
+    runs = {
+        "c3_lanczos_natural_order": (G3, dict(precision="mixed", degenerate_policy="none")),
+        "c3_lanczos_permuted": (H3, dict(precision="mixed", degenerate_policy="none")),
+        "c3_lanczos_permuted_rcb_reorder": (H3, dict(precision="mixed", degenerate_policy="none",
+                                                     reorder=1)),
+        "c3_lanczos_block2": (G3, dict(precision="mixed", degenerate_policy="none", block=2)),
+        "c3_inverse_cg": (G3, dict(method="inverse", precision="mixed", degenerate_policy="none",
+                                   reorder=1)),
+        "c3_inverse_amg_fcg": (G3, dict(method="inverse", amg=1, precision="mixed",
+                                        degenerate_policy="none", reorder=1)),
+    }
+    for name, (G, kw) in runs.items():
+        o = R.options(**kw)
+        R.rsb_partition(G, 2, o)
+        ms, (p, st, code) = _timed(torch, lambda: R.rsb_partition(G, 2, o), flush)
+        out[name] = {"ms_first_split": ms, "lambda2": st["lambda_first"], "cycles": st["cycles"],
+                     "cg_iterations": st["inner"], "status": code}
+    return out
 
 
 # ----------------------------------------------------------------------------

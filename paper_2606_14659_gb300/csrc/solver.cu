@@ -422,19 +422,45 @@ __global__ void __launch_bounds__(RSB_BLOCK) k_lz_c(LzArgs<V> a, int j, double b
 // the global timer): on timeout the CTA sets the grid error word, waits
 // (bounded) for its own copies still in flight and returns.
 // ----------------------------------------------------------------------------
+// The staged kernels walk a tile in chunks of ST_CH rows through ST_NB
+// buffers: while a chunk is being computed, the next ST_NB - 1 chunks are in
+// flight.  (Four buffers of 128 rows, for the same shared memory, were slower:
+// twice the copies for the same bytes.)  The copies of a chunk, one per basis
+// vector, are issued by the 32 lanes of warp 0 together.
+#define ST_CH 256
+#define ST_NB 2
+
 template <typename V>
 struct BulkRows {
   static constexpr int AL = 16 / sizeof(V);        // rows per 16 bytes
-  static constexpr int CRB = RSB_BLOCK + AL;       // staged rows per vector and buffer
+  static constexpr int CRB = ST_CH + AL;           // staged rows per vector and buffer
 };
 
 template <typename V>
 constexpr size_t lz_bt_smem(int nq) {
-  return 2 * (size_t)nq * BulkRows<V>::CRB * sizeof(V);
+  return ST_NB * (size_t)nq * BulkRows<V>::CRB * sizeof(V);
 }
 
-// Thread 0: rows [c0, c1) of q_0..q_{nq-1} (rounded out to 16 bytes) into
-// buffer b of Qb ([2][nq][CRB]), completing on bar[b].
+// Wait for chunk ci (buffer ci % ST_NB); false (uniform) when the copies did
+// not complete in time, after flagging the grid error word and draining this
+// CTA's copies still in flight (chunks ci .. ci + ST_NB - 1).
+__device__ __forceinline__ bool staged_wait(uint64_t* bar, int ci, int nchunk, GridBar* gb) {
+  const bool ok = mbar_wait_bounded(&bar[ci % ST_NB], (ci / ST_NB) & 1, 2000000000ull);
+  if (!__syncthreads_or(!ok)) return true;
+  if (threadIdx.x == 0) {
+    atomicMax(&gb->err, 1);
+    bool drained = true;
+    for (int c = ci; c < min(nchunk, ci + ST_NB); ++c)
+      drained = mbar_wait_bounded(&bar[c % ST_NB], (c / ST_NB) & 1, 1000000000ull) && drained;
+    if (!drained) atomicMax(&gb->err, 2);
+  }
+  __syncthreads();
+  return false;
+}
+
+// Warp 0 (all 32 lanes): rows [c0, c1) of q_0..q_{nq-1} (rounded out to 16
+// bytes) into buffer b of Qb ([ST_NB][slots][CRB]), completing on bar[b];
+// lane 0 registers the bytes, then lane l issues the copies of slots l, l + 32.
 // (extra, when given, is one more N-vector staged after q_{nq-1}; slots = nq
 // or nq + 1)
 template <typename V>
@@ -442,58 +468,62 @@ __device__ __forceinline__ void bulk_issue_chunk(const LzArgs<V>& a, V* Qb, uint
                                                  int b, int c0, int c1,
                                                  const V* extra = nullptr) {
   constexpr int AL = BulkRows<V>::AL, CRB = BulkRows<V>::CRB;
+  const int lane = threadIdx.x & 31;
   const int slots = nq + (extra ? 1 : 0);
   const int a0 = c0 & ~(AL - 1);
   const int len = (c1 - a0 + AL - 1) / AL * AL;
   const unsigned bytes = (unsigned)(len * sizeof(V));
   V* dst = Qb + (size_t)b * slots * CRB;
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-  mbar_expect_tx(&bar[b], bytes * (unsigned)slots);
-  for (int k = 0; k < nq; ++k)
-    bulk_g2s(dst + (size_t)k * CRB, a.Q + (long long)k * a.N + a0, bytes, &bar[b]);
-  if (extra) bulk_g2s(dst + (size_t)nq * CRB, extra + a0, bytes, &bar[b]);
+  if (lane == 0) mbar_expect_tx(&bar[b], bytes * (unsigned)slots);
+  __syncwarp();
+  for (int k = lane; k < slots; k += 32) {
+    const V* src = k < nq ? a.Q + (long long)k * a.N + a0 : extra + a0;
+    bulk_g2s(dst + (size_t)k * CRB, src, bytes, &bar[b]);
+  }
 }
 
 template <typename V>
 __global__ void __launch_bounds__(RSB_BLOCK, 2) k_lz_bt(LzArgs<V> a, int j, GridBar* gb) {
   extern __shared__ __align__(128) unsigned char bt_sh[];
   constexpr int AL = BulkRows<V>::AL, CRB = BulkRows<V>::CRB;
-  __shared__ __align__(8) uint64_t bar[2];
+  __shared__ __align__(8) uint64_t bar[ST_NB];
   __shared__ V ws[RSB_BLOCK];
   __shared__ V cv[RSB_MAXC];
   __shared__ double out[RSB_MAXC];
   const Tile t = a.tiles[blockIdx.x];
   Unit& u = a.units[t.unit];
   if (u.status != U_ACTIVE || j >= u.msteps || j < u.j0) return;
-  V* Qb = reinterpret_cast<V*>(bt_sh);  // [2][nq + 1][CRB]: q_0..q_j, then w
+  V* Qb = reinterpret_cast<V*>(bt_sh);  // [ST_NB][nq + 1][CRB]: q_0..q_j, then w
   const int nd = u.nd;
   const int nc = 2 + nd + j;
   const int nq = j + 1;
   V* w_ = (j & 1) ? a.W0 : a.W1;
-  const int nchunk = (t.row1 - t.row0 + RSB_BLOCK - 1) / RSB_BLOCK;
+  const int nchunk = (t.row1 - t.row0 + ST_CH - 1) / ST_CH;
   if (threadIdx.x == 0) {
-    mbar_init(&bar[0], 1);
-    mbar_init(&bar[1], 1);
+    for (int b = 0; b < ST_NB; ++b) mbar_init(&bar[b], 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   stage_coef<V, false>(u.c1, nc, u.isn, cv);  // ends with a CTA barrier
   // w is staged with the basis (its rows of a chunk are rewritten only after
   // that chunk's copies landed; rows the 16-byte rounding adds are not used)
-  if (threadIdx.x == 0)
-    bulk_issue_chunk(a, Qb, bar, nq, 0, t.row0, min(t.row1, t.row0 + RSB_BLOCK), (const V*)w_);
+  if (threadIdx.x < 32)
+    for (int c = 0; c < min(nchunk, ST_NB - 1); ++c)
+      bulk_issue_chunk(a, Qb, bar, nq, c, t.row0 + c * ST_CH,
+                       min(t.row1, t.row0 + (c + 1) * ST_CH), (const V*)w_);
   Acc<V> acc[MAXCW];
   unsigned long long pbytes = 0;
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   for (int ci = 0; ci < nchunk; ++ci) {
-    if (threadIdx.x == 0 && ci + 1 < nchunk) {
-      const int n0 = t.row0 + (ci + 1) * RSB_BLOCK;
-      bulk_issue_chunk(a, Qb, bar, nq, (ci + 1) & 1, n0, min(t.row1, n0 + RSB_BLOCK),
+    if (threadIdx.x < 32 && ci + ST_NB - 1 < nchunk) {
+      const int n0 = t.row0 + (ci + ST_NB - 1) * ST_CH;
+      bulk_issue_chunk(a, Qb, bar, nq, (ci + ST_NB - 1) % ST_NB, n0, min(t.row1, n0 + ST_CH),
                        (const V*)w_);
     }
-    if (!bulk_wait_chunk(bar, ci, nchunk, gb)) return;
-    const int c0 = t.row0 + ci * RSB_BLOCK;
-    const int c1 = min(t.row1, c0 + RSB_BLOCK);
-    const V* Qc = Qb + (size_t)(ci & 1) * (nq + 1) * CRB + (c0 - (c0 & ~(AL - 1)));
+    if (!staged_wait(bar, ci, nchunk, gb)) return;
+    const int c0 = t.row0 + ci * ST_CH;
+    const int c1 = min(t.row1, c0 + ST_CH);
+    const V* Qc = Qb + (size_t)(ci % ST_NB) * (nq + 1) * CRB + (c0 - (c0 & ~(AL - 1)));
     const int r = c0 + threadIdx.x;
     V wv = V(0);
     if (r < c1) {
@@ -561,12 +591,23 @@ __global__ void __launch_bounds__(RSB_BLOCK) k_lz_a1(LzArgs<V> a, int j) {
   V* dst = (j & 1) ? a.W0 : a.W1;
   V* qj = a.Q + (long long)j * a.N;
   unsigned long long pbytes = 0;
-#pragma unroll 4
-  for (int r = t.row0 + threadIdx.x; r < t.row1; r += RSB_BLOCK) {
-    const V xr = src[r];
-    dst[r] = s * spmv_row_ro<V>(a.slice_ptr, a.ent, src, r, xr);
+  // two rows per thread and pass (r and r + RSB_BLOCK) to keep more gathers in flight
+  for (int r = t.row0 + threadIdx.x; r < t.row1; r += 2 * RSB_BLOCK) {
+    const int r2 = r + RSB_BLOCK < t.row1 ? r + RSB_BLOCK : -1;
+    const V xr = __ldg(src + r);
+    const V xr2 = r2 >= 0 ? __ldg(src + r2) : V(0);
+    V y, y2;
+    spmv_2rows_ro<V>(a.slice_ptr, a.ent, src, r, r2, xr, xr2, y, y2);
+    dst[r] = s * y;
     qj[r] = s * xr;
-    if (a.pb_a) pbytes += 4ull * row_width(a.slice_ptr, r) + 3ull * sizeof(V);
+    if (r2 >= 0) {
+      dst[r2] = s * y2;
+      qj[r2] = s * xr2;
+    }
+    if (a.pb_a) {
+      pbytes += 4ull * row_width(a.slice_ptr, r) + 3ull * sizeof(V);
+      if (r2 >= 0) pbytes += 4ull * row_width(a.slice_ptr, r2) + 3ull * sizeof(V);
+    }
   }
   if (a.pb_a) prof_add(a.pb_a, pbytes);
 }
@@ -575,37 +616,40 @@ template <typename V>
 __global__ void __launch_bounds__(RSB_BLOCK, 2) k_lz_a2(LzArgs<V> a, int j, GridBar* gb) {
   extern __shared__ __align__(128) unsigned char a2_sh[];
   constexpr int AL = BulkRows<V>::AL, CRB = BulkRows<V>::CRB;
-  __shared__ __align__(8) uint64_t bar[2];
+  __shared__ __align__(8) uint64_t bar[ST_NB];
   __shared__ double out[RSB_MAXC];
   const Tile t = a.tiles[blockIdx.x];
   Unit& u = a.units[t.unit];
   if (u.status != U_ACTIVE || j >= u.msteps || j < u.j0) return;
-  V* Qb = reinterpret_cast<V*>(a2_sh);  // [2][j + 2][CRB]: q_0..q_j, then w
+  V* Qb = reinterpret_cast<V*>(a2_sh);  // [ST_NB][j + 2][CRB]: q_0..q_j, then w
   const int nd = u.nd;
   const int nc = 2 + nd + j;
   const int nq = j + 1;
   const int slots = nq + 1;
   const V* wsrc = (j & 1) ? a.W0 : a.W1;
-  const int nchunk = (t.row1 - t.row0 + RSB_BLOCK - 1) / RSB_BLOCK;
+  const int nchunk = (t.row1 - t.row0 + ST_CH - 1) / ST_CH;
   if (threadIdx.x == 0) {
-    mbar_init(&bar[0], 1);
-    mbar_init(&bar[1], 1);
+    for (int b = 0; b < ST_NB; ++b) mbar_init(&bar[b], 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    bulk_issue_chunk(a, Qb, bar, nq, 0, t.row0, min(t.row1, t.row0 + RSB_BLOCK), wsrc);
   }
   __syncthreads();
+  if (threadIdx.x < 32)
+    for (int c = 0; c < min(nchunk, ST_NB - 1); ++c)
+      bulk_issue_chunk(a, Qb, bar, nq, c, t.row0 + c * ST_CH,
+                       min(t.row1, t.row0 + (c + 1) * ST_CH), wsrc);
   Acc<V> acc[MAXCW];
   unsigned long long pbytes = 0;
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   for (int ci = 0; ci < nchunk; ++ci) {
-    if (threadIdx.x == 0 && ci + 1 < nchunk) {
-      const int n0 = t.row0 + (ci + 1) * RSB_BLOCK;
-      bulk_issue_chunk(a, Qb, bar, nq, (ci + 1) & 1, n0, min(t.row1, n0 + RSB_BLOCK), wsrc);
+    if (threadIdx.x < 32 && ci + ST_NB - 1 < nchunk) {
+      const int n0 = t.row0 + (ci + ST_NB - 1) * ST_CH;
+      bulk_issue_chunk(a, Qb, bar, nq, (ci + ST_NB - 1) % ST_NB, n0, min(t.row1, n0 + ST_CH),
+                       wsrc);
     }
-    if (!bulk_wait_chunk(bar, ci, nchunk, gb)) return;
-    const int c0 = t.row0 + ci * RSB_BLOCK;
-    const int c1 = min(t.row1, c0 + RSB_BLOCK);
-    const V* Qc = Qb + (size_t)(ci & 1) * slots * CRB + (c0 - (c0 & ~(AL - 1)));
+    if (!staged_wait(bar, ci, nchunk, gb)) return;
+    const int c0 = t.row0 + ci * ST_CH;
+    const int c1 = min(t.row1, c0 + ST_CH);
+    const V* Qc = Qb + (size_t)(ci % ST_NB) * slots * CRB + (c0 - (c0 & ~(AL - 1)));
     const V* ws = Qc + (size_t)nq * CRB;
     const int nr = c1 - c0;
     if (a.pb_a2 && (int)threadIdx.x < nr)
