@@ -118,8 +118,7 @@ __device__ __forceinline__ void final_reduce_b(const double* partials, long long
 
 // ----------------------------------------------------------------------------
 // chunk staging: rows [c0, c1) of q_0..q_{nq-1} (rounded out to 16 bytes) and
-// of the interleaved block Z into buffer b; warp 0 (lane 0 registers the
-// bytes, lane l issues the copies of slots l, l + 32, ...)
+// of the interleaved block Z into buffer b; thread 0 only
 // ----------------------------------------------------------------------------
 template <typename V>
 struct BStage {
@@ -138,14 +137,11 @@ __device__ __forceinline__ void stage_issue(const BlkArgs<V>& a, const V* Zc, V*
   const unsigned qbytes = (unsigned)(len * sizeof(V));
   const unsigned zbytes = (unsigned)((c1 - c0) * BZ * sizeof(V));
   V* dst = buf + (size_t)b * ((size_t)nq * CRB + ZR);
-  const int lane = threadIdx.x & 31;
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-  if (lane == 0) mbar_expect_tx(&bar[b], qbytes * (unsigned)nq + zbytes);
-  __syncwarp();
-  for (int k = lane; k <= nq; k += 32) {
-    if (k < nq) bulk_g2s(dst + (size_t)k * CRB, a.Q + (long long)k * a.N + a0, qbytes, &bar[b]);
-    else bulk_g2s(dst + (size_t)nq * CRB, Zc + (long long)c0 * BZ, zbytes, &bar[b]);
-  }
+  mbar_expect_tx(&bar[b], qbytes * (unsigned)nq + zbytes);
+  for (int k = 0; k < nq; ++k)
+    bulk_g2s(dst + (size_t)k * CRB, a.Q + (long long)k * a.N + a0, qbytes, &bar[b]);
+  bulk_g2s(dst + (size_t)nq * CRB, Zc + (long long)c0 * BZ, zbytes, &bar[b]);
 }
 
 // Coefficients of pass `pass` (0: c1, 1: c2) in the vector type:
@@ -358,13 +354,13 @@ __global__ void __launch_bounds__(RSB_BLOCK, 2) k_blk_gs(BlkArgs<V> a, int t) {
   if (MODE == 1) stage_coef_b<V, B>(bu.c1, nc, u.isn, cv);
   if (MODE == 2) stage_coef_b<V, B>(bu.c2, nc, u.isn, cv);
   __syncthreads();
-  if (threadIdx.x < 32)
+  if (threadIdx.x == 0)
     stage_issue(a, Zc, buf, bar, nq, 0, tl.row0, min(tl.row1, tl.row0 + RSB_BLOCK));
   Acc<V> acc[MAXCW][B];
   Acc<V> gacc[NG];
   unsigned long long pbytes = 0;
   for (int ci = 0; ci < nchunk; ++ci) {
-    if (threadIdx.x < 32 && ci + 1 < nchunk) {
+    if (threadIdx.x == 0 && ci + 1 < nchunk) {
       const int n0 = tl.row0 + (ci + 1) * RSB_BLOCK;
       stage_issue(a, Zc, buf, bar, nq, (ci + 1) & 1, n0, min(tl.row1, n0 + RSB_BLOCK));
     }

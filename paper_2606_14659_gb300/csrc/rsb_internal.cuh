@@ -209,49 +209,6 @@ __device__ __forceinline__ V spmv_row_ro(const int64_t* __restrict__ slice_ptr,
   return acc;
 }
 
-// Two rows at once (r1 < 0: only r0), the batches of both interleaved so that
-// up to sixteen gathers are in flight; each row's sum in its own entry order,
-// as spmv_row_ro.
-template <typename V>
-__device__ __forceinline__ void spmv_2rows_ro(const int64_t* __restrict__ slice_ptr,
-                                              const uint32_t* __restrict__ ent,
-                                              const V* __restrict__ x, int r0, int r1, V xr0,
-                                              V xr1, V& y0, V& y1) {
-  const int64_t b0 = slice_ptr[r0 >> 5];
-  const int w0 = (int)((slice_ptr[(r0 >> 5) + 1] - b0) >> 5);
-  int64_t b1 = 0;
-  int w1 = 0;
-  if (r1 >= 0) {
-    b1 = slice_ptr[r1 >> 5];
-    w1 = (int)((slice_ptr[(r1 >> 5) + 1] - b1) >> 5);
-  }
-  const uint32_t* e0 = ent + b0 + (r0 & 31);
-  const uint32_t* e1 = ent + b1 + (r1 & 31);
-  V a0 = V(0), a1 = V(0);
-  const int wm = max(w0, w1);
-  for (int k0 = 0; k0 < wm; k0 += 8) {
-    uint32_t p0[8], p1[8];
-#pragma unroll
-    for (int i = 0; i < 8; ++i) {
-      p0[i] = k0 + i < w0 ? __ldg(e0 + 32 * (k0 + i)) : 0u;
-      p1[i] = k0 + i < w1 ? __ldg(e1 + 32 * (k0 + i)) : 0u;
-    }
-    V x0[8], x1[8];
-#pragma unroll
-    for (int i = 0; i < 8; ++i) {
-      x0[i] = k0 + i < w0 ? __ldg(x + ent_col(p0[i])) : xr0;
-      x1[i] = k0 + i < w1 ? __ldg(x + ent_col(p1[i])) : xr1;
-    }
-#pragma unroll
-    for (int i = 0; i < 8; ++i) {
-      if (k0 + i < w0) a0 += V(ent_w(p0[i])) * (xr0 - x0[i]);
-      if (k0 + i < w1) a1 += V(ent_w(p1[i])) * (xr1 - x1[i]);
-    }
-  }
-  y0 = a0;
-  y1 = a1;
-}
-
 // Row membership in a unit.
 __device__ __forceinline__ bool unit_has(const Unit& u, const uint64_t* ckey, int r) {
   return !u.masked || ckey[r] == u.key;

@@ -424,9 +424,10 @@ __global__ void __launch_bounds__(RSB_BLOCK) k_lz_c(LzArgs<V> a, int j, double b
 // ----------------------------------------------------------------------------
 // The staged kernels walk a tile in chunks of ST_CH rows through ST_NB
 // buffers: while a chunk is being computed, the next ST_NB - 1 chunks are in
-// flight.  (Four buffers of 128 rows, for the same shared memory, were slower:
-// twice the copies for the same bytes.)  The copies of a chunk, one per basis
-// vector, are issued by the 32 lanes of warp 0 together.
+// flight.  Thread 0 issues the copies of a chunk, one per basis vector.
+// (Measured slower on GB300: four buffers of 128 rows for the same shared
+// memory, twice the copies for the same bytes; and the copies issued by the
+// 32 lanes of a warp together.)
 #define ST_CH 256
 #define ST_NB 2
 
@@ -458,9 +459,8 @@ __device__ __forceinline__ bool staged_wait(uint64_t* bar, int ci, int nchunk, G
   return false;
 }
 
-// Warp 0 (all 32 lanes): rows [c0, c1) of q_0..q_{nq-1} (rounded out to 16
-// bytes) into buffer b of Qb ([ST_NB][slots][CRB]), completing on bar[b];
-// lane 0 registers the bytes, then lane l issues the copies of slots l, l + 32.
+// Thread 0: rows [c0, c1) of q_0..q_{nq-1} (rounded out to 16 bytes) into
+// buffer b of Qb ([ST_NB][slots][CRB]), completing on bar[b].
 // (extra, when given, is one more N-vector staged after q_{nq-1}; slots = nq
 // or nq + 1)
 template <typename V>
@@ -468,19 +468,16 @@ __device__ __forceinline__ void bulk_issue_chunk(const LzArgs<V>& a, V* Qb, uint
                                                  int b, int c0, int c1,
                                                  const V* extra = nullptr) {
   constexpr int AL = BulkRows<V>::AL, CRB = BulkRows<V>::CRB;
-  const int lane = threadIdx.x & 31;
   const int slots = nq + (extra ? 1 : 0);
   const int a0 = c0 & ~(AL - 1);
   const int len = (c1 - a0 + AL - 1) / AL * AL;
   const unsigned bytes = (unsigned)(len * sizeof(V));
   V* dst = Qb + (size_t)b * slots * CRB;
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-  if (lane == 0) mbar_expect_tx(&bar[b], bytes * (unsigned)slots);
-  __syncwarp();
-  for (int k = lane; k < slots; k += 32) {
-    const V* src = k < nq ? a.Q + (long long)k * a.N + a0 : extra + a0;
-    bulk_g2s(dst + (size_t)k * CRB, src, bytes, &bar[b]);
-  }
+  mbar_expect_tx(&bar[b], bytes * (unsigned)slots);
+  for (int k = 0; k < nq; ++k)
+    bulk_g2s(dst + (size_t)k * CRB, a.Q + (long long)k * a.N + a0, bytes, &bar[b]);
+  if (extra) bulk_g2s(dst + (size_t)nq * CRB, extra + a0, bytes, &bar[b]);
 }
 
 template <typename V>
@@ -507,7 +504,7 @@ __global__ void __launch_bounds__(RSB_BLOCK, 2) k_lz_bt(LzArgs<V> a, int j, Grid
   stage_coef<V, false>(u.c1, nc, u.isn, cv);  // ends with a CTA barrier
   // w is staged with the basis (its rows of a chunk are rewritten only after
   // that chunk's copies landed; rows the 16-byte rounding adds are not used)
-  if (threadIdx.x < 32)
+  if (threadIdx.x == 0)
     for (int c = 0; c < min(nchunk, ST_NB - 1); ++c)
       bulk_issue_chunk(a, Qb, bar, nq, c, t.row0 + c * ST_CH,
                        min(t.row1, t.row0 + (c + 1) * ST_CH), (const V*)w_);
@@ -515,7 +512,7 @@ __global__ void __launch_bounds__(RSB_BLOCK, 2) k_lz_bt(LzArgs<V> a, int j, Grid
   unsigned long long pbytes = 0;
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   for (int ci = 0; ci < nchunk; ++ci) {
-    if (threadIdx.x < 32 && ci + ST_NB - 1 < nchunk) {
+    if (threadIdx.x == 0 && ci + ST_NB - 1 < nchunk) {
       const int n0 = t.row0 + (ci + ST_NB - 1) * ST_CH;
       bulk_issue_chunk(a, Qb, bar, nq, (ci + ST_NB - 1) % ST_NB, n0, min(t.row1, n0 + ST_CH),
                        (const V*)w_);
@@ -591,23 +588,13 @@ __global__ void __launch_bounds__(RSB_BLOCK) k_lz_a1(LzArgs<V> a, int j) {
   V* dst = (j & 1) ? a.W0 : a.W1;
   V* qj = a.Q + (long long)j * a.N;
   unsigned long long pbytes = 0;
-  // two rows per thread and pass (r and r + RSB_BLOCK) to keep more gathers in flight
-  for (int r = t.row0 + threadIdx.x; r < t.row1; r += 2 * RSB_BLOCK) {
-    const int r2 = r + RSB_BLOCK < t.row1 ? r + RSB_BLOCK : -1;
-    const V xr = __ldg(src + r);
-    const V xr2 = r2 >= 0 ? __ldg(src + r2) : V(0);
-    V y, y2;
-    spmv_2rows_ro<V>(a.slice_ptr, a.ent, src, r, r2, xr, xr2, y, y2);
-    dst[r] = s * y;
+  // (two rows per thread at once, sixteen gathers in flight, measured slower)
+#pragma unroll 4
+  for (int r = t.row0 + threadIdx.x; r < t.row1; r += RSB_BLOCK) {
+    const V xr = src[r];
+    dst[r] = s * spmv_row_ro<V>(a.slice_ptr, a.ent, src, r, xr);
     qj[r] = s * xr;
-    if (r2 >= 0) {
-      dst[r2] = s * y2;
-      qj[r2] = s * xr2;
-    }
-    if (a.pb_a) {
-      pbytes += 4ull * row_width(a.slice_ptr, r) + 3ull * sizeof(V);
-      if (r2 >= 0) pbytes += 4ull * row_width(a.slice_ptr, r2) + 3ull * sizeof(V);
-    }
+    if (a.pb_a) pbytes += 4ull * row_width(a.slice_ptr, r) + 3ull * sizeof(V);
   }
   if (a.pb_a) prof_add(a.pb_a, pbytes);
 }
@@ -633,7 +620,7 @@ __global__ void __launch_bounds__(RSB_BLOCK, 2) k_lz_a2(LzArgs<V> a, int j, Grid
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
-  if (threadIdx.x < 32)
+  if (threadIdx.x == 0)
     for (int c = 0; c < min(nchunk, ST_NB - 1); ++c)
       bulk_issue_chunk(a, Qb, bar, nq, c, t.row0 + c * ST_CH,
                        min(t.row1, t.row0 + (c + 1) * ST_CH), wsrc);
@@ -641,7 +628,7 @@ __global__ void __launch_bounds__(RSB_BLOCK, 2) k_lz_a2(LzArgs<V> a, int j, Grid
   unsigned long long pbytes = 0;
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   for (int ci = 0; ci < nchunk; ++ci) {
-    if (threadIdx.x < 32 && ci + ST_NB - 1 < nchunk) {
+    if (threadIdx.x == 0 && ci + ST_NB - 1 < nchunk) {
       const int n0 = t.row0 + (ci + ST_NB - 1) * ST_CH;
       bulk_issue_chunk(a, Qb, bar, nq, (ci + ST_NB - 1) % ST_NB, n0, min(t.row1, n0 + ST_CH),
                        wsrc);
