@@ -630,9 +630,9 @@ def next_rows(R, g5, dev, flush):
                                                      reorder=1)),
         "c3_lanczos_block2": (G3, dict(precision="mixed", degenerate_policy="none", block=2)),
         "c3_inverse_cg": (G3, dict(method="inverse", precision="mixed", degenerate_policy="none",
-                                   reorder=1)),
+                                   reorder=1, polish_cycles=8)),
         "c3_inverse_amg_fcg": (G3, dict(method="inverse", amg=1, precision="mixed",
-                                        degenerate_policy="none", reorder=1)),
+                                        degenerate_policy="none", reorder=1, polish_cycles=8)),
     }
     for name, (G, kw) in runs.items():
         o = R.options(**kw)

@@ -5,7 +5,7 @@
 //   * connected components of every segment (the multiplicity of the zero
 //     eigenvalue, §4, decides how a half that fell apart is split),
 //   * compaction: the induced subgraphs of both halves become the next level
-//     (Algorithm 1, "recurse on two halves"),
+//     (Algorithm 1: each half is bisected again),
 //   * weighted cut of a candidate split (the quantity the spectral relaxation
 //     of §3 minimises) and the part-id output.
 #include "rsb_internal.cuh"

@@ -1,6 +1,5 @@
-// select.cu — the median split of Algorithm 1 ("sort mesh elements according
-// to y2, assign the first half ... to the first half of processors", §4) done
-// as a selection instead of a sort:
+// select.cu — the median split of Algorithm 1 (§4), done as a selection
+// instead of the sort the paper describes:
 //   * orientation of the Fiedler vector (reading R4: the smallest gid among
 //     |v| >= max|v|/2 must come out negative),
 //   * a segmented 8-bit-digit radix select of the k-th smallest key per unit

@@ -75,3 +75,19 @@ def test_amg_reduces_inner_iterations():
                                           degenerate_policy="none", reorder=1))[1]
     assert amg["inner"] < plain["inner"] / 2, (amg["inner"], plain["inner"])
     assert abs(amg["lambda_first"] - plain["lambda_first"]) <= 1e-9 * plain["lambda_first"]
+
+
+def test_amg_c3_first_split_vs_oracle():
+    """The 192x128x96 mesh with 10 % deleted, in RCB order, first split by
+    AMG-FCG inverse iteration: the oracle's lambda_2 and cut (stored by
+    tests/golden/make_golden.py)."""
+    gold = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "c3_levels01.json")))
+    g = box_graph_deleted(192, 128, 96, 0.10, 20260, "vertex")
+    o = R.options(method="inverse", amg=1, precision="mixed", degenerate_policy="none",
+                  reorder=1, polish_cycles=8)
+    part, st, code = R.rsb_partition(R.graph(g), 2, o)
+    assert code == 0
+    lam0 = gold["splits"][0]["lambda2"]
+    assert abs(st["lambda_first"] - lam0) <= 1e-6 * lam0, (st["lambda_first"], lam0)
+    cut = O.weighted_cut(g, part.cpu().numpy() == 0)
+    assert abs(cut - gold["weighted_cut_2"]) <= 0.02 * gold["weighted_cut_2"]
