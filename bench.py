@@ -671,11 +671,36 @@ def case_main(args):
         print(f"spmv {args.dims} {args.adjacency} {'f32' if f32 else 'f64'}: {ms:.4f} ms, "
               f"{by / ms / 1e6:.0f} GB/s")
     else:
-        part, st, code = R.rsb_partition(G, args.parts, R.options(
-            precision=args.precision, use_graph=args.launch if args.launch is not None else 3))
+        # the headline's options on a smaller mesh: one warm run, one run inside
+        # the NVTX range "case_step" (what a launch list selects), then one run
+        # with every kernel family timed, whose shares the launch list should
+        # reproduce
+        o = R.options(precision=args.precision, method="lanczos", degenerate_policy="none",
+                      use_graph=args.launch if args.launch is not None else 1)
+        R.rsb_partition(G, args.parts, o)
         torch.cuda.synchronize()
+        torch.cuda.nvtx.range_push("case_step")
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        part, st, code = R.rsb_partition(G, args.parts, o)
+        e1.record()
+        e1.synchronize()
+        torch.cuda.nvtx.range_pop()
         print(f"partition {args.dims} -> {args.parts}: {st['levels']} levels, "
-              f"{st['kernel_launches']} launches, code {code}")
+              f"{st['kernel_launches']} launches, {e0.elapsed_time(e1):.1f} ms, code {code}")
+        R.rsb_profile_begin("all")
+        e0.record()
+        R.rsb_partition(G, args.parts, o)
+        e1.record()
+        e1.synchronize()
+        R.rsb_profile_end()
+        step_ms = e0.elapsed_time(e1)
+        for name in FAMILIES:
+            ms, nl, by = R.rsb_profile_read(name)
+            if nl:
+                print(f"  family {name}: {nl} launches, {ms:.2f} ms, share {ms / step_ms:.3f}, "
+                      f"{by / (ms * 1e6):.0f} GB/s")
     return 0
 
 

@@ -181,12 +181,26 @@ __device__ __forceinline__ double dkey_inv(uint64_t k) {
   return __longlong_as_double((long long)b);
 }
 
+// An entry's weight (0..7) as an exact double built with integer operations
+// (2^e (1 + m 2^-e) for w = 2^e + m), so that the FP64 Laplacian spends one FP64
+// instruction per entry: GB300 retires about two FP64 operations per SM cycle.
+__device__ __forceinline__ double weight_f64(uint32_t w) {
+  const int e = 31 - __clz((int)(w | 1u));
+  const unsigned long long m = (unsigned long long)(w - (1u << e)) << (52 - e);
+  const unsigned long long bits = ((unsigned long long)(1023 + e) << 52) | m;
+  return __longlong_as_double(w ? (long long)bits : 0ll);
+}
+
 // Laplacian action of one row, y_r = sum_k w_rk (x_r - x_{c_k}) in entry order
 // (the order every other form of the action uses, so the results are the same
 // bit for bit), for x that no thread of the launch writes: the row's entries
 // are loaded eight at a time and their gathers issued together through the
 // read-only path, so each thread keeps up to eight gathers in flight.
 // Entries past the row's width are neither loaded nor gathered.
+// In FP64 the row is d_r x_r - sum_k w_rk x_{c_k} (d_r = sum of the weights,
+// exact): one FMA per entry, with a rounding error of about 1e-16 d_r |x| that
+// FP64 can afford; FP32 keeps the differences, which are exact for close
+// values and avoid the cancellation on smooth vectors.
 template <typename V>
 __device__ __forceinline__ V spmv_row_ro(const int64_t* __restrict__ slice_ptr,
                                          const uint32_t* __restrict__ ent,
@@ -195,6 +209,7 @@ __device__ __forceinline__ V spmv_row_ro(const int64_t* __restrict__ slice_ptr,
   const int width = (int)((slice_ptr[(r >> 5) + 1] - base) >> 5);
   const uint32_t* e = ent + base + (r & 31);
   V acc = V(0);
+  uint32_t dsum = 0;
   for (int k0 = 0; k0 < width; k0 += 8) {
     uint32_t p[8];
 #pragma unroll
@@ -204,8 +219,16 @@ __device__ __forceinline__ V spmv_row_ro(const int64_t* __restrict__ slice_ptr,
     for (int i = 0; i < 8; ++i) xv[i] = k0 + i < width ? __ldg(x + ent_col(p[i])) : xr;
 #pragma unroll
     for (int i = 0; i < 8; ++i)
-      if (k0 + i < width) acc += V(ent_w(p[i])) * (xr - xv[i]);
+      if (k0 + i < width) {
+        if constexpr (sizeof(V) == 8) {
+          acc = fma(weight_f64(ent_w(p[i])), xv[i], acc);
+          dsum += ent_w(p[i]);
+        } else {
+          acc += V(ent_w(p[i])) * (xr - xv[i]);
+        }
+      }
   }
+  if constexpr (sizeof(V) == 8) return fma((double)dsum, xr, -acc);
   return acc;
 }
 

@@ -25,6 +25,7 @@
 // Precision: V = double (plain FP64) or V = float (vectors, SpMV and updates
 // in FP32; per-thread Kahan sums in FP32; CTA and cross-CTA sums, the
 // Gram-Schmidt coefficients, T, and the CG alpha/beta recurrences in FP64).
+#include <chrono>
 #include <algorithm>
 #include <cfloat>
 
@@ -82,11 +83,18 @@ __device__ __forceinline__ V spmv_row(const int64_t* __restrict__ slice_ptr,
   const int width = (int)((slice_ptr[(r >> 5) + 1] - base) >> 5);
   const uint32_t* e = ent + base + (r & 31);
   V acc = V(0);
+  uint32_t dsum = 0;
 #pragma unroll 4
   for (int k = 0; k < width; ++k) {
     const uint32_t p = __ldg(e + 32 * k);
-    acc += V(ent_w(p)) * (xr - ldc<CO>(x + ent_col(p)));
+    if constexpr (sizeof(V) == 8) {  // FP64: d_r x_r - sum w x_c, as spmv_row_ro
+      acc = fma(weight_f64(ent_w(p)), ldc<CO>(x + ent_col(p)), acc);
+      dsum += ent_w(p);
+    } else {
+      acc += V(ent_w(p)) * (xr - ldc<CO>(x + ent_col(p)));
+    }
   }
+  if constexpr (sizeof(V) == 8) return fma((double)dsum, xr, -acc);
   return acc;
 }
 
@@ -426,8 +434,9 @@ __global__ void __launch_bounds__(RSB_BLOCK) k_lz_c(LzArgs<V> a, int j, double b
 // buffers: while a chunk is being computed, the next ST_NB - 1 chunks are in
 // flight.  Thread 0 issues the copies of a chunk, one per basis vector.
 // (Measured slower on GB300: four buffers of 128 rows for the same shared
-// memory, twice the copies for the same bytes; and the copies issued by the
-// 32 lanes of a warp together.)
+// memory, twice the copies for the same bytes; the copies issued by the 32
+// lanes of a warp together; and an L2 bulk prefetch of the chunks two ahead of
+// the copies.)
 #define ST_CH 256
 #define ST_NB 2
 
@@ -480,6 +489,14 @@ __device__ __forceinline__ void bulk_issue_chunk(const LzArgs<V>& a, V* Qb, uint
   if (extra) bulk_g2s(dst + (size_t)nq * CRB, extra + a0, bytes, &bar[b]);
 }
 
+// Thread 0 of a staged kernel: the copies of chunk c into its buffer.
+template <typename V>
+__device__ __forceinline__ void stage_chunk(const LzArgs<V>& a, V* Qb, uint64_t* bar, int nq,
+                                            const Tile& t, int c, const V* extra = nullptr) {
+  const int n0 = t.row0 + c * ST_CH;
+  bulk_issue_chunk(a, Qb, bar, nq, c % ST_NB, n0, min(t.row1, n0 + ST_CH), extra);
+}
+
 template <typename V>
 __global__ void __launch_bounds__(RSB_BLOCK, 2) k_lz_bt(LzArgs<V> a, int j, GridBar* gb) {
   extern __shared__ __align__(128) unsigned char bt_sh[];
@@ -512,11 +529,8 @@ __global__ void __launch_bounds__(RSB_BLOCK, 2) k_lz_bt(LzArgs<V> a, int j, Grid
   unsigned long long pbytes = 0;
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   for (int ci = 0; ci < nchunk; ++ci) {
-    if (threadIdx.x == 0 && ci + ST_NB - 1 < nchunk) {
-      const int n0 = t.row0 + (ci + ST_NB - 1) * ST_CH;
-      bulk_issue_chunk(a, Qb, bar, nq, (ci + ST_NB - 1) % ST_NB, n0, min(t.row1, n0 + ST_CH),
-                       (const V*)w_);
-    }
+    if (threadIdx.x == 0 && ci + ST_NB - 1 < nchunk)
+      stage_chunk(a, Qb, bar, nq, t, ci + ST_NB - 1, (const V*)w_);
     if (!staged_wait(bar, ci, nchunk, gb)) return;
     const int c0 = t.row0 + ci * ST_CH;
     const int c1 = min(t.row1, c0 + ST_CH);
@@ -575,10 +589,20 @@ __global__ void __launch_bounds__(RSB_BLOCK, 2) k_lz_bt(LzArgs<V> a, int j, Grid
 // written to global memory.  A2: the first-pass dots [1, D, q_0..q_j]^T w with
 // q_0..q_j and w staged chunk by chunk in shared memory by bulk copies, as in
 // step B.  Together they compute what lz_a_t computes, in the same order.
+// A CTA takes A1_RPT * RSB_BLOCK consecutive rows of a tile (CTA b: tile
+// b / nsub, part b % nsub of it), A1_RPT rows per thread.
+#ifndef A1_RPT
+#define A1_RPT 4
+#endif
 template <typename V>
-__global__ void __launch_bounds__(RSB_BLOCK) k_lz_a1(LzArgs<V> a, int j) {
+__global__ void __launch_bounds__(RSB_BLOCK) k_lz_a1(LzArgs<V> a, int j, int nsub) {
   __shared__ double scale;
-  const Tile t = a.tiles[blockIdx.x];
+  const int tix = (int)(blockIdx.x / (unsigned)nsub);
+  const Tile t = a.tiles[tix];
+  const long long p0 = (long long)t.row0 +
+                       (long long)(blockIdx.x - (unsigned)tix * nsub) * (A1_RPT * RSB_BLOCK);
+  if (p0 >= t.row1) return;
+  const int p1 = (int)min((long long)t.row1, p0 + A1_RPT * RSB_BLOCK);
   const Unit& u = a.units[t.unit];
   if (u.status != U_ACTIVE || j >= u.msteps || j < u.j0) return;
   if (threadIdx.x == 0) scale = 1.0 / (j == u.j0 ? u.beta0 : u.beta[j]);
@@ -588,9 +612,8 @@ __global__ void __launch_bounds__(RSB_BLOCK) k_lz_a1(LzArgs<V> a, int j) {
   V* dst = (j & 1) ? a.W0 : a.W1;
   V* qj = a.Q + (long long)j * a.N;
   unsigned long long pbytes = 0;
-  // (two rows per thread at once, sixteen gathers in flight, measured slower)
 #pragma unroll 4
-  for (int r = t.row0 + threadIdx.x; r < t.row1; r += RSB_BLOCK) {
+  for (int r = (int)p0 + threadIdx.x; r < p1; r += RSB_BLOCK) {
     const V xr = src[r];
     dst[r] = s * spmv_row_ro<V>(a.slice_ptr, a.ent, src, r, xr);
     qj[r] = s * xr;
@@ -628,11 +651,8 @@ __global__ void __launch_bounds__(RSB_BLOCK, 2) k_lz_a2(LzArgs<V> a, int j, Grid
   unsigned long long pbytes = 0;
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   for (int ci = 0; ci < nchunk; ++ci) {
-    if (threadIdx.x == 0 && ci + ST_NB - 1 < nchunk) {
-      const int n0 = t.row0 + (ci + ST_NB - 1) * ST_CH;
-      bulk_issue_chunk(a, Qb, bar, nq, (ci + ST_NB - 1) % ST_NB, n0, min(t.row1, n0 + ST_CH),
-                       wsrc);
-    }
+    if (threadIdx.x == 0 && ci + ST_NB - 1 < nchunk)
+      stage_chunk(a, Qb, bar, nq, t, ci + ST_NB - 1, wsrc);
     if (!staged_wait(bar, ci, nchunk, gb)) return;
     const int c0 = t.row0 + ci * ST_CH;
     const int c1 = min(t.row1, c0 + ST_CH);
@@ -1559,11 +1579,13 @@ static int lz_start(LzArgs<V>& a, int ntiles, uint64_t sd, const double* from64,
 
 template <typename V>
 static int lz_cycle(LzArgs<V>& a, int ntiles, int nunits, int M, double breakdown, GridBar* gb,
-                    cudaStream_t s) {
+                    int trmax, cudaStream_t s) {
+  // CTAs per tile of step A1
+  const int nsub = std::max(1, (trmax + A1_RPT * RSB_BLOCK - 1) / (A1_RPT * RSB_BLOCK));
   for (int j = 0; j < M; ++j) {
     int pi = prof_before(PROF_LZ_A, s);
     if (sizeof(V) == 4) {
-      k_lz_a1<V><<<ntiles, RSB_BLOCK, 0, s>>>(a, j);
+      k_lz_a1<V><<<ntiles * nsub, RSB_BLOCK, 0, s>>>(a, j, nsub);
       RSB_CKL("k_lz_a1");
       prof_after(pi, s);
       pi = prof_before(PROF_LZ_A2, s);
@@ -1609,6 +1631,8 @@ static int lanczos_run(const LevelGraph& G, const Tile* tiles, int ntiles, Unit*
                        const double* from64, const float* from32, int use_graph,
                        cudaStream_t s) {
   LzArgs<V> a = make_args<V>(G, tiles, ntiles, units, ckey, B);
+  // step A1 and the resident kernel size their launches by the largest tile
+  if (B.trmax <= 0) return rsb_set_error(RSB_EINVAL, "Lanczos solve without its largest tile size");
   int active = 0;
   int rc = read_active(B, s, &active);
   if (rc || active == 0) return rc;
@@ -1622,7 +1646,7 @@ static int lanczos_run(const LevelGraph& G, const Tile* tiles, int ntiles, Unit*
     if (g_rsb_poison_barrier && (use_graph == 2 || use_graph == 3))
       RSB_CK(cudaMemsetAsync(&B.gb->count, 0x40, sizeof(unsigned int), s));
   }
-  if (use_graph == 3 && B.gb && B.trmax > 0) {
+  if (use_graph == 3 && B.gb) {
     // the whole solve in one cooperative launch when every tile gets a
     // co-resident CTA holding its rows of the basis; otherwise CUDA graphs
     int dev = 0, nsm = 0, optin = 0, occ = 0;
@@ -1694,7 +1718,7 @@ static int lanczos_run(const LevelGraph& G, const Tile* tiles, int ntiles, Unit*
     cudaGraph_t graph = nullptr;
     RSB_CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
     prof_capture_begin();
-    rc = lz_cycle<V>(a, ntiles, nunits, M, breakdown, B.gb, s);
+    rc = lz_cycle<V>(a, ntiles, nunits, M, breakdown, B.gb, B.trmax, s);
     cap_pairs = prof_capture_end();
     cudaGraph_t g2 = nullptr;
     cudaError_t e = cudaStreamEndCapture(s, &g2);
@@ -1708,6 +1732,9 @@ static int lanczos_run(const LevelGraph& G, const Tile* tiles, int ntiles, Unit*
     cudaGraphDestroy(graph);
     if (e != cudaSuccess) return rsb_set_cuda_error(e, "cudaGraphInstantiate");
   }
+  const char* tr = getenv("RSB_TRACE");
+  const bool trace = tr && *tr && *tr != '0';
+  auto t_prev = std::chrono::steady_clock::now();
   for (int cyc = 0; cyc < 100000; ++cyc) {
     if (exec) {
       cudaError_t e = cudaGraphLaunch(exec, s);
@@ -1718,10 +1745,17 @@ static int lanczos_run(const LevelGraph& G, const Tile* tiles, int ntiles, Unit*
       }
       prof_replay(cap_pairs);
     } else {
-      rc = lz_cycle<V>(a, ntiles, nunits, M, breakdown, B.gb, s);
+      rc = lz_cycle<V>(a, ntiles, nunits, M, breakdown, B.gb, B.trmax, s);
       if (rc) return rc;
     }
     rc = read_active(B, s, &active);
+    if (trace) {  // per-cycle wall time and units still active (RSB_TRACE=1)
+      const auto now = std::chrono::steady_clock::now();
+      fprintf(stderr, "[rsb]   %9.3f ms    cycle %d: %d of %d units active\n",
+              std::chrono::duration<double, std::milli>(now - t_prev).count(), cyc, active,
+              nunits);
+      t_prev = now;
+    }
     if (rc || active == 0) break;
   }
   if (exec) cudaGraphExecDestroy(exec);
@@ -2138,6 +2172,8 @@ static int inverse_run(const LevelGraph& G, const Tile* tiles, int ntiles, Unit*
                        int use_graph, int64_t* inner_out, cudaStream_t s,
                        const std::vector<Unit>* amg_units) {
   LzArgs<V> a = make_args<V>(G, tiles, ntiles, units, ckey, B);
+  // step A1 and the resident kernel size their launches by the largest tile
+  if (B.trmax <= 0) return rsb_set_error(RSB_EINVAL, "Lanczos solve without its largest tile size");
   int active = 0;
   int rc = read_active(B, s, &active);
   if (rc || active == 0) return rc;
