@@ -286,17 +286,17 @@ def aggregate(total_ms: float, units: float, dist=None, device=None):
 # ----------------------------------------------------------------------------
 LAUNCH_NAMES = ["kernels", "cuda_graph", "persistent_cycle", "persistent_resident"]
 FAMILIES = {
-    "lz_a": "k_lz_a1 (FP32 Lanczos step A: SpMV w = L q_j of the sliced-ELL graph, q_j = w / beta)",
-    "lz_a2": ("k_lz_a2 (FP32 Lanczos step A: first Gram-Schmidt dots of w with the basis, "
-              "staged in shared memory by bulk copies)"),
-    "lz_b": ("k_lz_bt (FP32 Lanczos step B: w -= Q c1 and second Gram-Schmidt dots, basis "
-             "staged by bulk copies)"),
-    "lz_c": "k_lz_c (FP32 Lanczos step C: w -= Q c2 and ||w||)",
+    "lz_a": "k_lz_a1 (FP32 Lanczos step D1: SpMV z = L v_j of the sliced-ELL graph, v_j = w_j / nu_j)",
+    "lz_a2": ("k_lz_d2 (FP32 Lanczos step D2: dots of v_j and z with the basis in one pass, the "
+              "basis, v_j and z staged in shared memory by bulk copies)"),
+    "lz_b": ("k_lz_d3 (FP32 Lanczos step D3: q_j = (v_j - B a) / rho and w_{j+1} = (z - B g - "
+             "(q_j.z) q_j) / rho in one pass over the basis, ||w_{j+1}||)"),
+    "lz_c": "k_lz_c (FP64 Lanczos step C: w -= Q c2 and ||w||)",
     "cg_ap": "k_cg_ap (CG: Ap = L p and p.Ap)",
     "cycle": ("k_lz_res (one cooperative launch per Fiedler solve: SpMV, CGS2 against the "
               "shared-memory-resident basis, Jacobi Ritz pairs, thick restart)"),
 }
-PROFILE_KERNEL = {"lz_a": "k_lz_a1", "lz_a2": "k_lz_a2", "lz_b": "k_lz_bt", "lz_c": "k_lz_c",
+PROFILE_KERNEL = {"lz_a": "k_lz_a1", "lz_a2": "k_lz_d2", "lz_b": "k_lz_d3", "lz_c": "k_lz_c",
                   "cg_ap": "k_cg_ap", "cycle": "k_lz_res"}
 
 
@@ -355,7 +355,8 @@ def our_arm(args):
     Gs = [R.graph(g, device=dev) for g in gs]
     n_total = sum(g.n for g in gs)
     opts = R.options(precision=args.precision, batched=1,
-                     use_graph=args.launch if args.launch is not None else 3, **W["opts"])
+                     use_graph=args.launch if args.launch is not None else 3,
+                     tile_rows=args.tile_rows, **W["opts"])
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     outs = [torch.empty(g.n, dtype=torch.int32, device=dev) for g in gs]
     tuned = None
@@ -720,6 +721,9 @@ def main():
                     help="fix the Lanczos launch mode (0 kernels, 1 CUDA graph per cycle, "
                          "2 persistent kernel per cycle, 3 resident persistent kernel per "
                          "solve) instead of autotuning it with the tile rows")
+    ap.add_argument("--tile-rows", type=int, default=0,
+                    help="minimum rows per thread of a tile when --launch fixes the launch mode "
+                         "(0: the library's default)")
     ap.add_argument("--quick", action="store_true", help="skip the CPU baseline")
     ap.add_argument("--case", choices=["lanczos", "spmv", "partition"], default=None,
                     help="run one small fixed case (for ncu) instead of the benchmark")

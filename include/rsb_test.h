@@ -20,13 +20,14 @@ extern "C" {
  * library's stream and add up the algorithmic bytes of each launch;
  * rsb_profile_end() returns the totals over the timed families and switches
  * timing off; rsb_profile_read() then gives one family's totals.  Families:
- *   1 Lanczos step A: the SpMV launch k_lz_a1 (FP32) or the fused k_lz_a (FP64)
- *   2 step B (update + second Gram-Schmidt dots)
- *   3 step C (update + norm)
+ *   1 Lanczos SpMV: k_lz_a1 (FP32 step D1) or the fused k_lz_a (FP64 step A)
+ *   2 FP32 step D3 (both updates + norm, k_lz_d3) or FP64 step B (update +
+ *     second Gram-Schmidt dots, k_lz_b)
+ *   3 FP64 step C (update + norm, k_lz_c)
  *   4 CG Laplacian action (inverse iteration)
  *   5 Laplacian action of rsb_laplacian_bench
  *   6 the persistent Lanczos kernels (bytes of all of their phases)
- *   7 FP32 step A's first Gram-Schmidt dots, k_lz_a2
+ *   7 FP32 step D2 (dots of v_j and z with the basis, k_lz_d2)
  *   8 the AMG V-cycles of the flexible CG (time only)
  * Bytes count 4 B per stored SELL entry (padding included), every vector
  * element read or written once, and FP64 deflation vectors.  The event

@@ -92,6 +92,7 @@ struct Unit {
   // CG scalars (§7): FP64 recurrences in both precisions
   double rr, cg_alpha, cg_beta, bnorm;
   double fz_rz, fz_ro;          // flexible CG: z.r and z.r_old of the new z
+  double dz_src, dz_z, dz_qz;   // delayed second pass: scales of src, z and q_j in step D3
   double cz[1 + RSB_MAXD];      // flexible CG: projection coefficients of z
   double rq, lnorm2;
   // select / split

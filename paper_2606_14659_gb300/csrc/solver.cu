@@ -1,20 +1,27 @@
 // solver.cu — Fiedler solvers of librsb, batched over all units of a level.
 //
-// Lanczos with restarts (paper §6): per step
-//   A: w = L q_j - beta_j q_{j-1}, fused with the first Gram-Schmidt pass's
-//      dot products against [1/sqrt(n), deflation vectors, q_0..q_j]
-//      (alpha_j is the coefficient on q_j),
+// Lanczos with restarts (paper §6), the Lanczos vectors kept orthonormal by
+// classical Gram-Schmidt with a second pass (CGS2).  FP64 steps:
+//   A: w = L q_j, fused with the first Gram-Schmidt pass's dot products
+//      against [1/sqrt(n), deflation vectors, q_0..q_j],
 //   B: w -= basis * c1, fused with the second pass's dot products,
-//   C: w -= basis * c2, fused with ||w||^2 -> beta_{j+1}.
+//   C: w -= basis * c2, fused with ||w||^2 -> beta_{j+1};
 // q_{j+1} = w / beta_{j+1} is materialised by the next step's A, which gathers
-// the unnormalised w and scales.  After the cycle: the Ritz pairs of the
+// the unnormalised w and scales.  FP32 steps (bandwidth-bound) delay the
+// second pass by one step, two passes over the basis instead of three:
+//   D1: z = L v_j (v_j = w_j / nu_j, projected once),
+//   D2: a = B^T v_j, g = B^T z, v.v, v.z in one pass -> q_j = (v_j - B a) / rho
+//       and column j of S,
+//   D3: q_j and w_{j+1} = (z - B g - (q_j.z) q_j) / rho in one pass, nu_{j+1}.
+// After the cycle: the Ritz pairs of the
 // projected matrix S = Q^T L Q (parallel cyclic Jacobi, one CTA per unit), the
 // Ritz vector y = Q t, the true residual ||L y - theta y||, and a thick restart
 // from the kept Ritz vectors and the last residual direction (an explicit
 // restart from y, projected against the fixed basis, when a cycle ended on an
 // invariant subspace).  Launch modes: one kernel per step phase (optionally
-// replayed as a CUDA graph per cycle), one cooperative kernel per cycle, or one
-// cooperative kernel per solve with the basis resident in shared memory.
+// replayed as a CUDA graph per cycle), one cooperative kernel per cycle (CGS2
+// in both precisions), or one cooperative kernel per solve with the basis
+// resident in shared memory (the steps of the per-phase kernels, bit for bit).
 //
 // Inverse iteration (paper §7, Algorithm 2): the right-hand side b is the
 // projected, normalised previous iterate; L x = b is solved by CG from x0 = 0
@@ -419,15 +426,12 @@ __global__ void __launch_bounds__(RSB_BLOCK) k_lz_c(LzArgs<V> a, int j, double b
 }
 
 // ----------------------------------------------------------------------------
-// Step B with the basis staged by TMA (launch modes 0 and 1).  The tile is
-// walked in chunks of RSB_BLOCK rows; for every chunk one thread issues 1-D
-// bulk copies (cp.async.bulk, completion counted in bytes on an mbarrier) of
-// the chunk's rows of q_0..q_j into shared memory, one chunk ahead of the one
-// being computed (two buffers).  The update and the second-pass dots then
-// read the basis from shared memory, so DRAM sees each basis vector once per
-// launch.  The per-row update order and the per-lane dot order are those of
-// lz_b_t and the resident kernel.  Waits on the mbarrier are bounded (2 s of
-// the global timer): on timeout the CTA sets the grid error word, waits
+// Bulk-copy staging (launch modes 0 and 1, FP32 step D2).  The tile is walked
+// in chunks of ST_CH rows; for every chunk one thread issues 1-D bulk copies
+// (cp.async.bulk, completion counted in bytes on an mbarrier) of the chunk's
+// rows of the basis (and of the step's work vectors) into shared memory, one
+// chunk ahead of the one being computed.  Waits on the mbarrier are bounded
+// (2 s of the global timer): on timeout the CTA sets the grid error word, waits
 // (bounded) for its own copies still in flight and returns.
 // ----------------------------------------------------------------------------
 // The staged kernels walk a tile in chunks of ST_CH rows through ST_NB
@@ -447,7 +451,7 @@ struct BulkRows {
 };
 
 template <typename V>
-constexpr size_t lz_bt_smem(int nq) {
+constexpr size_t staged_smem(int nq) {
   return ST_NB * (size_t)nq * BulkRows<V>::CRB * sizeof(V);
 }
 
@@ -470,14 +474,15 @@ __device__ __forceinline__ bool staged_wait(uint64_t* bar, int ci, int nchunk, G
 
 // Thread 0: rows [c0, c1) of q_0..q_{nq-1} (rounded out to 16 bytes) into
 // buffer b of Qb ([ST_NB][slots][CRB]), completing on bar[b].
-// (extra, when given, is one more N-vector staged after q_{nq-1}; slots = nq
-// or nq + 1)
+// (extra and extra2, when given, are N-vectors staged after q_{nq-1}; slots =
+// nq plus the extras given)
 template <typename V>
 __device__ __forceinline__ void bulk_issue_chunk(const LzArgs<V>& a, V* Qb, uint64_t* bar, int nq,
                                                  int b, int c0, int c1,
-                                                 const V* extra = nullptr) {
+                                                 const V* extra = nullptr,
+                                                 const V* extra2 = nullptr) {
   constexpr int AL = BulkRows<V>::AL, CRB = BulkRows<V>::CRB;
-  const int slots = nq + (extra ? 1 : 0);
+  const int slots = nq + (extra ? 1 : 0) + (extra2 ? 1 : 0);
   const int a0 = c0 & ~(AL - 1);
   const int len = (c1 - a0 + AL - 1) / AL * AL;
   const unsigned bytes = (unsigned)(len * sizeof(V));
@@ -486,110 +491,22 @@ __device__ __forceinline__ void bulk_issue_chunk(const LzArgs<V>& a, V* Qb, uint
   mbar_expect_tx(&bar[b], bytes * (unsigned)slots);
   for (int k = 0; k < nq; ++k)
     bulk_g2s(dst + (size_t)k * CRB, a.Q + (long long)k * a.N + a0, bytes, &bar[b]);
-  if (extra) bulk_g2s(dst + (size_t)nq * CRB, extra + a0, bytes, &bar[b]);
+  int k = nq;
+  if (extra) bulk_g2s(dst + (size_t)(k++) * CRB, extra + a0, bytes, &bar[b]);
+  if (extra2) bulk_g2s(dst + (size_t)k * CRB, extra2 + a0, bytes, &bar[b]);
 }
 
 // Thread 0 of a staged kernel: the copies of chunk c into its buffer.
 template <typename V>
 __device__ __forceinline__ void stage_chunk(const LzArgs<V>& a, V* Qb, uint64_t* bar, int nq,
-                                            const Tile& t, int c, const V* extra = nullptr) {
+                                            const Tile& t, int c, const V* extra = nullptr,
+                                            const V* extra2 = nullptr) {
   const int n0 = t.row0 + c * ST_CH;
-  bulk_issue_chunk(a, Qb, bar, nq, c % ST_NB, n0, min(t.row1, n0 + ST_CH), extra);
+  bulk_issue_chunk(a, Qb, bar, nq, c % ST_NB, n0, min(t.row1, n0 + ST_CH), extra, extra2);
 }
 
-template <typename V>
-__global__ void __launch_bounds__(RSB_BLOCK, 2) k_lz_bt(LzArgs<V> a, int j, GridBar* gb) {
-  extern __shared__ __align__(128) unsigned char bt_sh[];
-  constexpr int AL = BulkRows<V>::AL, CRB = BulkRows<V>::CRB;
-  __shared__ __align__(8) uint64_t bar[ST_NB];
-  __shared__ V ws[RSB_BLOCK];
-  __shared__ V cv[RSB_MAXC];
-  __shared__ double out[RSB_MAXC];
-  const Tile t = a.tiles[blockIdx.x];
-  Unit& u = a.units[t.unit];
-  if (u.status != U_ACTIVE || j >= u.msteps || j < u.j0) return;
-  V* Qb = reinterpret_cast<V*>(bt_sh);  // [ST_NB][nq + 1][CRB]: q_0..q_j, then w
-  const int nd = u.nd;
-  const int nc = 2 + nd + j;
-  const int nq = j + 1;
-  V* w_ = (j & 1) ? a.W0 : a.W1;
-  const int nchunk = (t.row1 - t.row0 + ST_CH - 1) / ST_CH;
-  if (threadIdx.x == 0) {
-    for (int b = 0; b < ST_NB; ++b) mbar_init(&bar[b], 1);
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-  }
-  stage_coef<V, false>(u.c1, nc, u.isn, cv);  // ends with a CTA barrier
-  // w is staged with the basis (its rows of a chunk are rewritten only after
-  // that chunk's copies landed; rows the 16-byte rounding adds are not used)
-  if (threadIdx.x == 0)
-    for (int c = 0; c < min(nchunk, ST_NB - 1); ++c)
-      bulk_issue_chunk(a, Qb, bar, nq, c, t.row0 + c * ST_CH,
-                       min(t.row1, t.row0 + (c + 1) * ST_CH), (const V*)w_);
-  Acc<V> acc[MAXCW];
-  unsigned long long pbytes = 0;
-  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  for (int ci = 0; ci < nchunk; ++ci) {
-    if (threadIdx.x == 0 && ci + ST_NB - 1 < nchunk)
-      stage_chunk(a, Qb, bar, nq, t, ci + ST_NB - 1, (const V*)w_);
-    if (!staged_wait(bar, ci, nchunk, gb)) return;
-    const int c0 = t.row0 + ci * ST_CH;
-    const int c1 = min(t.row1, c0 + ST_CH);
-    const V* Qc = Qb + (size_t)(ci % ST_NB) * (nq + 1) * CRB + (c0 - (c0 & ~(AL - 1)));
-    const int r = c0 + threadIdx.x;
-    V wv = V(0);
-    if (r < c1) {
-      wv = Qc[(size_t)nq * CRB + threadIdx.x];
-      if (unit_has(u, a.ckey, r)) wv -= cv[0];
-      for (int l = 0; l < nd; ++l) wv -= cv[1 + l] * V((l == 0 ? a.D0 : a.D1)[r]);
-      const V* cq = cv + 1 + nd;
-      for (int k = 0; k < nq; ++k) wv -= cq[k] * Qc[(size_t)k * CRB + threadIdx.x];
-      w_[r] = wv;
-      if (a.pb_b) pbytes += sizeof(V) * (unsigned long long)(3 + j) + 8ull * nd;
-    }
-    ws[threadIdx.x] = wv;
-    __syncthreads();
-    const int nr = c1 - c0;
-#pragma unroll
-    for (int i = 0; i < MAXCW; ++i) {
-      const int c = w + RSB_WARPS * i;
-      if (c < nc) {
-        if (c == 0) {
-          for (int rl = lane; rl < nr; rl += 32) acc[i].add(V(1) * ws[rl]);
-        } else if (c <= nd) {
-          const double* d = c == 1 ? a.D0 : a.D1;
-          for (int rl = lane; rl < nr; rl += 32) acc[i].add(V(d[c0 + rl]) * ws[rl]);
-        } else {
-          const V* q = Qc + (size_t)(c - 1 - nd) * CRB;
-          for (int rl = lane; rl < nr; rl += 32) acc[i].add(q[rl] * ws[rl]);
-        }
-      }
-    }
-    __syncthreads();
-  }
-  store_dots<V>(a, nc, acc, blockIdx.x);
-  if (a.pb_b) prof_add(a.pb_b, pbytes);
-  if (last_cta(&u.cnt, u.ntile)) {
-    final_reduce(a.partials, a.stride, u.tile0, u.ntile, nc, out);
-    if (threadIdx.x == 0) {
-      u.c2[0] = out[0] * u.isn;
-      for (int c = 1; c < nc; ++c) u.c2[c] = out[c];
-    }
-    __syncthreads();
-    double* Sm = unit_S(a.S, t.unit);
-    for (int k = threadIdx.x; k <= j; k += RSB_BLOCK) {
-      const double v = u.c1[1 + nd + k] + out[1 + nd + k];
-      Sm[k * RSB_MAXM + j] = v;
-      Sm[j * RSB_MAXM + k] = v;
-    }
-  }
-}
-
-// Step A of the FP32 streaming path in two launches.  A1: w = L q_j and
-// q_j = src / beta for every row (all of a thread's rows' gathers in flight),
-// written to global memory.  A2: the first-pass dots [1, D, q_0..q_j]^T w with
-// q_0..q_j and w staged chunk by chunk in shared memory by bulk copies, as in
-// step B.  Together they compute what lz_a_t computes, in the same order.
-// A CTA takes A1_RPT * RSB_BLOCK consecutive rows of a tile (CTA b: tile
+// Step D1 of the FP32 streaming path: z = L (src / nu_j) into the work vector
+// AP (src stays as it is: D2 and D3 read it).  A CTA takes A1_RPT * RSB_BLOCK consecutive rows of a tile (CTA b: tile
 // b / nsub, part b % nsub of it), A1_RPT rows per thread.
 #ifndef A1_RPT
 #define A1_RPT 4
@@ -609,34 +526,100 @@ __global__ void __launch_bounds__(RSB_BLOCK) k_lz_a1(LzArgs<V> a, int j, int nsu
   __syncthreads();
   const V s = V(scale);
   const V* src = (j & 1) ? a.W1 : a.W0;
-  V* dst = (j & 1) ? a.W0 : a.W1;
-  V* qj = a.Q + (long long)j * a.N;
+  V* z = a.AP;
   unsigned long long pbytes = 0;
 #pragma unroll 4
   for (int r = (int)p0 + threadIdx.x; r < p1; r += RSB_BLOCK) {
     const V xr = src[r];
-    dst[r] = s * spmv_row_ro<V>(a.slice_ptr, a.ent, src, r, xr);
-    qj[r] = s * xr;
-    if (a.pb_a) pbytes += 4ull * row_width(a.slice_ptr, r) + 3ull * sizeof(V);
+    z[r] = s * spmv_row_ro<V>(a.slice_ptr, a.ent, src, r, xr);
+    if (a.pb_a) pbytes += 4ull * row_width(a.slice_ptr, r) + 2ull * sizeof(V);
   }
   if (a.pb_a) prof_add(a.pb_a, pbytes);
 }
 
+// Closing arithmetic of step D2 for one unit (every thread of the CTA takes
+// part), from the reduced totals av = [a_b (b < nb), v.v] and gz = [g_b
+// (b < nb), v.z] of src, scaled here in place to v = src / nu (inu = 1 / nu)
+// and u0 = 1/sqrt(n) on its entry; sc[0..2] = rho, q_j.z, alpha and
+// sk[0..j) = S_kj come back in shared memory.  S is read for columns < j;
+// column and row j are written when write_s.  The streaming kernel and the
+// resident kernel both call this, so both modes produce the same numbers.
+template <bool CO>
+__device__ void d2_finish(double* av, double* gz, int nb, int nd, int j, double inu, double isn,
+                          double* Sm, bool write_s, double* sc, double* sk) {
+  if (threadIdx.x == 0) {
+    for (int b = 0; b < nb; ++b) av[b] *= inu;
+    av[nb] *= inu * inu;
+    gz[nb] *= inu;
+    av[0] *= isn;
+    gz[0] *= isn;
+    double aa = 0.0, ag = 0.0;
+    for (int b = 0; b < nb; ++b) {
+      aa += av[b] * av[b];
+      ag += av[b] * gz[b];
+    }
+    const double rho2 = av[nb] - aa;
+    // v has unit norm and |a| is at rounding level after its first pass; a
+    // non-positive rho^2 means v lies in span(B) to working precision
+    const double rho = rho2 > 0.0 ? sqrt(rho2) : 1e-300;
+    sc[0] = rho;
+    sc[1] = (gz[nb] - ag) / rho;  // q_j.z
+  }
+  __syncthreads();
+  const double rho = sc[0];
+  const double* aq = av + 1 + nd;  // a on q_0..q_{j-1}
+  for (int k = threadIdx.x; k < j; k += RSB_BLOCK) {
+    double sa_k = 0.0;
+    for (int i = 0; i < j; ++i) sa_k += ldc<CO>(Sm + k * RSB_MAXM + i) * aq[i];
+    sk[k] = (gz[1 + nd + k] - sa_k) / rho;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double sig = 0.0;
+    for (int k = 0; k < j; ++k) sig += sk[k] * aq[k];
+    sc[2] = (sc[1] - sig) / rho;
+    if (write_s) Sm[j * RSB_MAXM + j] = sc[2];
+  }
+  if (write_s)
+    for (int k = threadIdx.x; k < j; k += RSB_BLOCK) {
+      Sm[k * RSB_MAXM + j] = sk[k];
+      Sm[j * RSB_MAXM + k] = sk[k];
+    }
+  __syncthreads();
+}
+
+// ----------------------------------------------------------------------------
+// Step D2 of the FP32 streaming path (second Gram-Schmidt pass delayed by one
+// step, DCGS2: Swirydowicz, Langou, Ananthan, Yang and Thomas, "Low
+// synchronization Gram-Schmidt and GMRES algorithms", 2020).  v = src / nu_j
+// has been projected once against B = [u0, D, q_0..q_{j-1}]; z = L v (D1).
+// One staged pass over q_0..q_{j-1}, src and z takes a = B^T v, g = B^T z,
+// v.v and v.z; the unit's last CTA then forms
+//   rho = sqrt(v.v - a.a)                  q_j = (v - B a) / rho
+//   L q_j = (z - L B a) / rho, where L B a lies in span(B, q_j) up to
+//   rounding (L u0 = 0; D holds eigenvector approximations; L q_i for i < j
+//   is in span(q_0..q_j) by the Lanczos relation), so that
+//   S_kj = q_k.L q_j = (g_k - sum_i S_ki a_i) / rho           (k < j)
+//   S_jj = (q_j.z - sum_k S_kj a_k) / rho, q_j.z = (v.z - a.g) / rho,
+// and the coefficients of D3.  Partials: [a_b (b < nb), v.v] then
+// [g_b (b < nb), v.z], nb = 1 + nd + j.
+// ----------------------------------------------------------------------------
 template <typename V>
-__global__ void __launch_bounds__(RSB_BLOCK, 2) k_lz_a2(LzArgs<V> a, int j, GridBar* gb) {
-  extern __shared__ __align__(128) unsigned char a2_sh[];
+__global__ void __launch_bounds__(RSB_BLOCK, 2) k_lz_d2(LzArgs<V> a, int j, GridBar* gb) {
+  extern __shared__ __align__(128) unsigned char d2_sh[];
   constexpr int AL = BulkRows<V>::AL, CRB = BulkRows<V>::CRB;
   __shared__ __align__(8) uint64_t bar[ST_NB];
-  __shared__ double out[RSB_MAXC];
+  __shared__ double out[2 * RSB_MAXC + 2];
   const Tile t = a.tiles[blockIdx.x];
   Unit& u = a.units[t.unit];
   if (u.status != U_ACTIVE || j >= u.msteps || j < u.j0) return;
-  V* Qb = reinterpret_cast<V*>(a2_sh);  // [ST_NB][j + 2][CRB]: q_0..q_j, then w
+  V* Qb = reinterpret_cast<V*>(d2_sh);  // [ST_NB][j + 2][CRB]: q_0..q_{j-1}, src, z
   const int nd = u.nd;
-  const int nc = 2 + nd + j;
-  const int nq = j + 1;
-  const int slots = nq + 1;
-  const V* wsrc = (j & 1) ? a.W0 : a.W1;
+  const int nb = 1 + nd + j;  // columns of B
+  const int nc = nb + 1;      // plus v itself (v.v, v.z)
+  const int nq = j;
+  const int slots = nq + 2;
+  const V* src = (j & 1) ? a.W1 : a.W0;
   const int nchunk = (t.row1 - t.row0 + ST_CH - 1) / ST_CH;
   if (threadIdx.x == 0) {
     for (int b = 0; b < ST_NB; ++b) mbar_init(&bar[b], 1);
@@ -646,45 +629,185 @@ __global__ void __launch_bounds__(RSB_BLOCK, 2) k_lz_a2(LzArgs<V> a, int j, Grid
   if (threadIdx.x == 0)
     for (int c = 0; c < min(nchunk, ST_NB - 1); ++c)
       bulk_issue_chunk(a, Qb, bar, nq, c, t.row0 + c * ST_CH,
-                       min(t.row1, t.row0 + (c + 1) * ST_CH), wsrc);
-  Acc<V> acc[MAXCW];
+                       min(t.row1, t.row0 + (c + 1) * ST_CH), src, (const V*)a.AP);
+  Acc<V> av[MAXCW], az[MAXCW];
   unsigned long long pbytes = 0;
-  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   for (int ci = 0; ci < nchunk; ++ci) {
     if (threadIdx.x == 0 && ci + ST_NB - 1 < nchunk)
-      stage_chunk(a, Qb, bar, nq, t, ci + ST_NB - 1, wsrc);
+      stage_chunk(a, Qb, bar, nq, t, ci + ST_NB - 1, src, (const V*)a.AP);
     if (!staged_wait(bar, ci, nchunk, gb)) return;
     const int c0 = t.row0 + ci * ST_CH;
     const int c1 = min(t.row1, c0 + ST_CH);
     const V* Qc = Qb + (size_t)(ci % ST_NB) * slots * CRB + (c0 - (c0 & ~(AL - 1)));
-    const V* ws = Qc + (size_t)nq * CRB;
+    const V* vs = Qc + (size_t)nq * CRB;
+    const V* zs = vs + CRB;
     const int nr = c1 - c0;
     if (a.pb_a2 && (int)threadIdx.x < nr)
-      pbytes += sizeof(V) * (unsigned long long)(1 + j) + 8ull * nd;
+      pbytes += sizeof(V) * (unsigned long long)(2 + j) + 8ull * nd;
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
 #pragma unroll
     for (int i = 0; i < MAXCW; ++i) {
       const int c = w + RSB_WARPS * i;
       if (c < nc) {
         if (c == 0) {
-          for (int rl = lane; rl < nr; rl += 32) acc[i].add(V(1) * ws[rl]);
+          for (int rl = lane; rl < nr; rl += 32) {
+            av[i].add(vs[rl]);
+            az[i].add(zs[rl]);
+          }
         } else if (c <= nd) {
           const double* d = c == 1 ? a.D0 : a.D1;
-          for (int rl = lane; rl < nr; rl += 32) acc[i].add(V(d[c0 + rl]) * ws[rl]);
+          for (int rl = lane; rl < nr; rl += 32) {
+            const V dv = V(d[c0 + rl]);
+            av[i].add(dv * vs[rl]);
+            az[i].add(dv * zs[rl]);
+          }
         } else {
-          const V* q = Qc + (size_t)(c - 1 - nd) * CRB;
-          for (int rl = lane; rl < nr; rl += 32) acc[i].add(q[rl] * ws[rl]);
+          const V* q = c < nb ? Qc + (size_t)(c - 1 - nd) * CRB : vs;
+          for (int rl = lane; rl < nr; rl += 32) {
+            const V qv = q[rl];
+            av[i].add(qv * vs[rl]);
+            az[i].add(qv * zs[rl]);
+          }
         }
       }
     }
     __syncthreads();
   }
-  store_dots<V>(a, nc, acc, blockIdx.x);
+  store_dots<V>(a, nc, av, blockIdx.x);
+  {
+    LzArgs<V> a2 = a;
+    a2.partials = a.partials + (long long)nc * a.stride;
+    store_dots<V>(a2, nc, az, blockIdx.x);
+  }
   if (a.pb_a2) prof_add(a.pb_a2, pbytes);
   if (last_cta(&u.cnt, u.ntile)) {
     final_reduce(a.partials, a.stride, u.tile0, u.ntile, nc, out);
+    final_reduce(a.partials + (long long)nc * a.stride, a.stride, u.tile0, u.ntile, nc, out + nc);
+    const double inu = 1.0 / (j == u.j0 ? u.beta0 : u.beta[j]);
+    __shared__ double sc[3], sk[RSB_MAXM];
+    d2_finish<false>(out, out + nc, nb, nd, j, inu, u.isn, unit_S(a.S, t.unit), true, sc, sk);
+    const double rho = sc[0];
     if (threadIdx.x == 0) {
-      u.c1[0] = out[0] * u.isn;
-      for (int c = 1; c < nc; ++c) u.c1[c] = out[c];
+      u.alpha[j] = sc[2];
+      // D3: q_j = src / (nu rho) - sum_b (a_b / rho) b,
+      //     w = z / rho - sum_b (g_b / rho) b - (q_j.z / rho) q_j
+      u.dz_src = inu / rho;
+      u.dz_z = 1.0 / rho;
+      u.dz_qz = sc[1] / rho;
+    }
+    for (int b = threadIdx.x; b < nb; b += RSB_BLOCK) {
+      u.c2[b] = out[b] / rho;
+      u.c1[b] = out[nc + b] / rho;
+    }
+  }
+}
+
+// Step D3 of the FP32 streaming path: per row, q_j = src / (nu rho) - B a~ and
+// w_{j+1} = z / rho - B g~ - (q_j.z / rho) q_j (a~ = a / rho, g~ = g / rho;
+// one pass over the basis, two updates per loaded value); q_j goes to the
+// basis, w_{j+1} to the other work vector, nu_{j+1} = ||w_{j+1}||.
+template <typename V>
+__global__ void __launch_bounds__(RSB_BLOCK) k_lz_d3(LzArgs<V> a, int j, double breakdown) {
+  __shared__ double sm[RSB_WARPS];
+  __shared__ V ca[RSB_MAXC], cg[RSB_MAXC];
+  __shared__ double out[1];
+  const Tile t = a.tiles[blockIdx.x];
+  Unit& u = a.units[t.unit];
+  if (u.status != U_ACTIVE || j >= u.msteps || j < u.j0) return;
+  const int nd = u.nd;
+  const int nb = 1 + nd + j;
+  stage_coef<V, false>(u.c2, nb, u.isn, ca);
+  stage_coef<V, false>(u.c1, nb, u.isn, cg);
+  const V ssrc = V(u.dz_src), sz = V(u.dz_z), sqz = V(u.dz_qz);
+  const V* src = (j & 1) ? a.W1 : a.W0;
+  V* dst = (j & 1) ? a.W0 : a.W1;
+  const V* z = a.AP;
+  V* qj = a.Q + (long long)j * a.N;
+  Acc<V> acc;
+  unsigned long long pbytes = 0;
+  for (int base = t.row0; base < t.row1; base += SUBROWS) {
+    const int end = min(t.row1, base + SUBROWS);
+    V q[RSB_SUBR], w[RSB_SUBR];
+    bool ok[RSB_SUBR];
+#pragma unroll
+    for (int rr = 0; rr < RSB_SUBR; ++rr) {
+      const int r = base + rr * RSB_BLOCK + threadIdx.x;
+      ok[rr] = r < end;
+      q[rr] = ok[rr] ? ssrc * src[r] : V(0);
+      w[rr] = ok[rr] ? sz * z[r] : V(0);
+      if (ok[rr] && unit_has(u, a.ckey, r)) {
+        q[rr] -= ca[0];
+        w[rr] -= cg[0];
+      }
+    }
+    for (int l = 0; l < nd; ++l) {
+      const double* d = l == 0 ? a.D0 : a.D1;
+#pragma unroll
+      for (int rr = 0; rr < RSB_SUBR; ++rr) {
+        const int r = base + rr * RSB_BLOCK + threadIdx.x;
+        if (ok[rr]) {
+          const V dv = V(d[r]);
+          q[rr] -= ca[1 + l] * dv;
+          w[rr] -= cg[1 + l] * dv;
+        }
+      }
+    }
+    const V* cqa = ca + 1 + nd;
+    const V* cqg = cg + 1 + nd;
+    int k = 0;
+    for (; k + 4 <= j; k += 4) {  // four basis vectors per round
+      V qv[4][RSB_SUBR];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const V* qk = a.Q + (long long)(k + i) * a.N + base + threadIdx.x;
+#pragma unroll
+        for (int rr = 0; rr < RSB_SUBR; ++rr) qv[i][rr] = ok[rr] ? qk[rr * RSB_BLOCK] : V(0);
+      }
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const V ka = cqa[k + i], kg = cqg[k + i];
+#pragma unroll
+        for (int rr = 0; rr < RSB_SUBR; ++rr) {
+          q[rr] -= ka * qv[i][rr];
+          w[rr] -= kg * qv[i][rr];
+        }
+      }
+    }
+    for (; k < j; ++k) {
+      const V ka = cqa[k], kg = cqg[k];
+      const V* qk = a.Q + (long long)k * a.N + base + threadIdx.x;
+#pragma unroll
+      for (int rr = 0; rr < RSB_SUBR; ++rr)
+        if (ok[rr]) {
+          const V b = qk[rr * RSB_BLOCK];
+          q[rr] -= ka * b;
+          w[rr] -= kg * b;
+        }
+    }
+#pragma unroll
+    for (int rr = 0; rr < RSB_SUBR; ++rr) {
+      const int r = base + rr * RSB_BLOCK + threadIdx.x;
+      if (ok[rr]) {
+        w[rr] -= sqz * q[rr];
+        qj[r] = q[rr];
+        dst[r] = w[rr];
+        acc.add(w[rr] * w[rr]);
+        if (a.pb_b) pbytes += sizeof(V) * (unsigned long long)(4 + j) + 8ull * nd;
+      }
+    }
+  }
+  if (a.pb_b) prof_add(a.pb_b, pbytes);
+  const double sum = block_total(acc, sm);
+  if (threadIdx.x == 0) a.partials[blockIdx.x] = sum;
+  if (last_cta(&u.cnt, u.ntile)) {
+    final_reduce(a.partials, a.stride, u.tile0, u.ntile, 1, out);
+    if (threadIdx.x == 0) {
+      const double b = sqrt(out[0]);
+      u.beta[j + 1] = b;
+      if (b <= breakdown * u.dmax) {  // invariant subspace: the cycle ends here
+        u.msteps = j + 1;
+        u.broke = 1;
+      }
     }
   }
 }
@@ -1146,15 +1269,16 @@ __global__ void __launch_bounds__(RSB_BLOCK, 2)
 // operand, the reduction partials and the per-unit scalars.  Steps, their
 // order, the per-thread accumulation order and the reductions are those of
 // the streaming kernels above, so both modes give the same numbers.
-// Shared layout: JacShared | coefficients (FP64, and in the vector type) | w of
-// the tile | deflation vectors of the tile | Q[k * trs + rl].
+// Shared layout: JacShared | coefficients (FP64, and in the vector type) | w
+// (z) of the tile | v of the tile (FP32) | deflation vectors of the tile |
+// Q[k * trs + rl].
 // ----------------------------------------------------------------------------
 __host__ __device__ constexpr size_t res_align(size_t b) { return (b + 15) & ~(size_t)15; }
 
 template <typename V>
 __host__ __device__ constexpr size_t res_smem_bytes(int M, int trs) {
   return res_align(sizeof(JacShared<V>)) + res_align(2 * sizeof(double) * RSB_MAXC) +
-         res_align(2 * sizeof(V) * RSB_MAXC) + res_align(sizeof(V) * (size_t)trs) +
+         res_align(2 * sizeof(V) * RSB_MAXC) + 2 * res_align(sizeof(V) * (size_t)trs) +
          res_align(sizeof(V) * RSB_MAXD * (size_t)trs) + sizeof(V) * (size_t)M * (size_t)trs;
 }
 
@@ -1282,6 +1406,108 @@ __device__ void res_c(const LzArgs<V>& a, int j, int tix, const Tile& t, int nd,
   if (threadIdx.x == 0) P[tix] = sum;
 }
 
+// FP32 steps with the delayed second pass (D1-D3 of the streaming kernels,
+// in their order).  D1(j): v = src rows into vs, z = L (src / nu) into ws.
+template <typename V>
+__device__ void res_d1(const LzArgs<V>& a, int j, V s, const Tile& t, V* vs, V* ws) {
+  const int nr = t.row1 - t.row0;
+  const V* src = (j & 1) ? a.W1 : a.W0;
+  unsigned long long pbytes = 0;
+  for (int rl = threadIdx.x; rl < nr; rl += RSB_BLOCK) {
+    const int r = t.row0 + rl;
+    const V xr = __ldcg(src + r);
+    vs[rl] = xr;
+    ws[rl] = s * spmv_row<V, true>(a.slice_ptr, a.ent, src, r, xr);
+    if (a.pb_a) pbytes += 4ull * row_width(a.slice_ptr, r) + 2ull * sizeof(V);
+  }
+  if (a.pb_a) prof_add(a.pb_a, pbytes);
+  __syncthreads();
+}
+
+// D2(j): dots of v (vs) and z (ws) with [1, D, q_0..q_{j-1}] and with v, in the
+// per-lane order of k_lz_d2 (partials [a_b, v.v] then [g_b, v.z]).
+template <typename V>
+__device__ void res_d2(const LzArgs<V>& a, int j, int tix, const Tile& t, int nd, const V* Qs,
+                       const V* Ds, int trs, const V* vs, const V* ws, double* P) {
+  const int nr = t.row1 - t.row0;
+  const int nb = 1 + nd + j;
+  const int nc = nb + 1;
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  Acc<V> av[MAXCW], az[MAXCW];
+#pragma unroll
+  for (int i = 0; i < MAXCW; ++i) {
+    const int c = w + RSB_WARPS * i;
+    if (c < nc) {
+      if (c == 0) {
+        for (int rl = lane; rl < nr; rl += 32) {
+          av[i].add(vs[rl]);
+          az[i].add(ws[rl]);
+        }
+      } else if (c <= nd) {
+        const V* d = Ds + (size_t)(c - 1) * trs;
+        for (int rl = lane; rl < nr; rl += 32) {
+          av[i].add(d[rl] * vs[rl]);
+          az[i].add(d[rl] * ws[rl]);
+        }
+      } else {
+        const V* q = c < nb ? Qs + (size_t)(c - 1 - nd) * trs : vs;
+        for (int rl = lane; rl < nr; rl += 32) {
+          const V qv = q[rl];
+          av[i].add(qv * vs[rl]);
+          az[i].add(qv * ws[rl]);
+        }
+      }
+    }
+  }
+  res_store_dots<V>(P, a.stride, nc, av, tix);
+  res_store_dots<V>(P + (long long)nc * a.stride, a.stride, nc, az, tix);
+  if (a.pb_a2) {
+    unsigned long long pbytes = 0;
+    for (int rl = threadIdx.x; rl < nr; rl += RSB_BLOCK)
+      pbytes += sizeof(V) * (unsigned long long)(2 + j) + 8ull * nd;
+    prof_add(a.pb_a2, pbytes);
+  }
+}
+
+// D3(j): q_j = ssrc v - B ca into Qs, w = sz z - B cg - sqz q_j into
+// W[(j + 1) & 1], ||w||^2 (the per-row order of k_lz_d3).
+template <typename V>
+__device__ void res_d3(const LzArgs<V>& a, int j, int tix, const Tile& t, int nd, bool masked,
+                       uint64_t key, V* Qs, const V* Ds, int trs, const V* vs, const V* ws,
+                       const V* ca, const V* cg, V ssrc, V sz, V sqz, double* sm, double* P) {
+  const int nr = t.row1 - t.row0;
+  V* dst = (j & 1) ? a.W0 : a.W1;
+  Acc<V> acc;
+  unsigned long long pbytes = 0;
+  for (int rl = threadIdx.x; rl < nr; rl += RSB_BLOCK) {
+    const bool in_unit = !masked || a.ckey[t.row0 + rl] == key;
+    V q = ssrc * vs[rl];
+    V w = sz * ws[rl];
+    if (in_unit) {
+      q -= ca[0];
+      w -= cg[0];
+    }
+    for (int l = 0; l < nd; ++l) {
+      const V dv = Ds[(size_t)l * trs + rl];
+      q -= ca[1 + l] * dv;
+      w -= cg[1 + l] * dv;
+    }
+    for (int k = 0; k < j; ++k) {
+      const V b = Qs[(size_t)k * trs + rl];
+      q -= ca[1 + nd + k] * b;
+      w -= cg[1 + nd + k] * b;
+    }
+    w -= sqz * q;
+    Qs[(size_t)j * trs + rl] = q;
+    dst[t.row0 + rl] = w;
+    acc.add(w * w);
+    if (a.pb_b) pbytes += sizeof(V) * (unsigned long long)(4 + j) + 8ull * nd;
+  }
+  if (a.pb_b) prof_add(a.pb_b, pbytes);
+  const double sum = block_total(acc, sm);
+  if (threadIdx.x == 0) P[tix] = sum;
+}
+
 // coefficients of a finished reduction: c[0] carries the 1/sqrt(n) of u0 (as
 // the streaming kernels store it); cv the same in the vector type, cv[0]
 // already times 1/sqrt(n) again (the u0 component of the update)
@@ -1347,10 +1573,13 @@ __global__ void __launch_bounds__(RSB_BLOCK, 2)
   off += res_align(2 * sizeof(V) * RSB_MAXC);
   V* ws = reinterpret_cast<V*>(res_sh + off);
   off += res_align(sizeof(V) * (size_t)trs);
+  V* vs = reinterpret_cast<V*>(res_sh + off);
+  off += res_align(sizeof(V) * (size_t)trs);
   V* Ds = reinterpret_cast<V*>(res_sh + off);
   off += res_align(sizeof(V) * RSB_MAXD * (size_t)trs);
   V* Qs = reinterpret_cast<V*>(res_sh + off);
-  __shared__ double out[RSB_MAXC];
+  __shared__ double out[2 * RSB_MAXC + 2];
+  __shared__ double dsc[3], dsk[RSB_MAXM];
   __shared__ double sm[RSB_WARPS];
   __shared__ double beta_sh;
   __shared__ V scale_sh;
@@ -1389,6 +1618,54 @@ __global__ void __launch_bounds__(RSB_BLOCK, 2)
     int ph = 0;
     for (int j = jstart; j < M; ++j) {
       const bool st = on && j < msteps && j >= j0;
+      if constexpr (sizeof(V) == 4) {
+        // FP32: the streaming kernels' steps D1-D3 (second pass delayed);
+        // partials: D2 in rows [0, 2 nc), the norm in row 2 RSB_MAXC, so that
+        // no CTA rewrites rows another CTA of the unit may still reduce
+        const int nb = 1 + nd + j;
+        const int nc = nb + 1;
+        double* Pn = a.partials + (long long)(2 * RSB_MAXC) * a.stride;
+        if (st) {
+          res_d1<V>(a, j, scale_sh, t, vs, ws);
+          res_d2<V>(a, j, tix, t, nd, Qs, Ds, trs, vs, ws, a.partials);
+        }
+        if (!grid_sync(gb, G)) return;
+        if (st) {
+          final_reduce(a.partials, a.stride, u.tile0, u.ntile, nc, out);
+          final_reduce(a.partials + (long long)nc * a.stride, a.stride, u.tile0, u.ntile, nc,
+                       out + nc);
+          const double inu = 1.0 / beta_sh;
+          d2_finish<true>(out, out + nc, nb, nd, j, inu, isn, unit_S(a.S, t.unit),
+                          tix == u.tile0, dsc, dsk);
+          const double rho = dsc[0];
+          for (int k = threadIdx.x; k < nb; k += RSB_BLOCK) {
+            const double ck = out[k] / rho, gk = out[nc + k] / rho;
+            cv2[k] = k == 0 ? V(ck * isn) : V(ck);
+            cv1[k] = k == 0 ? V(gk * isn) : V(gk);
+          }
+          if (lead) u.alpha[j] = dsc[2];
+          __syncthreads();
+          res_d3<V>(a, j, tix, t, nd, masked, key, Qs, Ds, trs, vs, ws, cv2, cv1, V(inu / rho),
+                    V(1.0 / rho), V(dsc[1] / rho), sm, Pn);
+        }
+        if (!grid_sync(gb, G)) return;
+        if (st) {
+          final_reduce(Pn, a.stride, u.tile0, u.ntile, 1, out);
+          if (threadIdx.x == 0) {
+            const double b = sqrt(out[0]);
+            beta_sh = b;
+            scale_sh = V(1.0 / b);
+            if (lead) u.beta[j + 1] = b;
+            if (b <= breakdown * u.dmax && lead) {  // invariant subspace: the cycle ends here
+              u.msteps = j + 1;
+              u.broke = 1;
+            }
+          }
+          __syncthreads();
+          if (beta_sh <= breakdown * u.dmax) msteps = j + 1;
+        }
+        continue;
+      }
       const int nc = 2 + nd + j;
       if (st) res_a<V>(a, j, scale_sh, tix, t, u, Qs, Ds, trs, ws, Pb[ph & 1]);
       if (!grid_sync(gb, G)) return;
@@ -1584,26 +1861,27 @@ static int lz_cycle(LzArgs<V>& a, int ntiles, int nunits, int M, double breakdow
   const int nsub = std::max(1, (trmax + A1_RPT * RSB_BLOCK - 1) / (A1_RPT * RSB_BLOCK));
   for (int j = 0; j < M; ++j) {
     int pi = prof_before(PROF_LZ_A, s);
-    if (sizeof(V) == 4) {
+    if constexpr (sizeof(V) == 4) {  // FP32: bandwidth-bound; CGS2 with the second pass delayed
       k_lz_a1<V><<<ntiles * nsub, RSB_BLOCK, 0, s>>>(a, j, nsub);
       RSB_CKL("k_lz_a1");
       prof_after(pi, s);
       pi = prof_before(PROF_LZ_A2, s);
-      k_lz_a2<V><<<ntiles, RSB_BLOCK, lz_bt_smem<V>(j + 2), s>>>(a, j, gb);
-      RSB_CKL("k_lz_a2");
-    } else {
-      k_lz_a<V><<<ntiles, RSB_BLOCK, 0, s>>>(a, j);
-      RSB_CKL("k_lz_a");
+      k_lz_d2<V><<<ntiles, RSB_BLOCK, staged_smem<V>(j + 2), s>>>(a, j, gb);
+      RSB_CKL("k_lz_d2");
+      prof_after(pi, s);
+      pi = prof_before(PROF_LZ_B, s);
+      k_lz_d3<V><<<ntiles, RSB_BLOCK, 0, s>>>(a, j, breakdown);
+      RSB_CKL("k_lz_d3");
+      prof_after(pi, s);
+      continue;
     }
+    // FP64: bound by GB300's FP64 rate; register-streaming kernels, CGS2
+    k_lz_a<V><<<ntiles, RSB_BLOCK, 0, s>>>(a, j);
+    RSB_CKL("k_lz_a");
     prof_after(pi, s);
     pi = prof_before(PROF_LZ_B, s);
-    if (sizeof(V) == 4) {  // FP32: bandwidth-bound, basis staged by bulk copies
-      k_lz_bt<V><<<ntiles, RSB_BLOCK, lz_bt_smem<V>(j + 2), s>>>(a, j, gb);
-      RSB_CKL("k_lz_bt");
-    } else {  // FP64: bound by GB300's FP64 rate; the register-streaming kernel is faster
-      k_lz_b<V><<<ntiles, RSB_BLOCK, 0, s>>>(a, j);
-      RSB_CKL("k_lz_b");
-    }
+    k_lz_b<V><<<ntiles, RSB_BLOCK, 0, s>>>(a, j);
+    RSB_CKL("k_lz_b");
     prof_after(pi, s);
     pi = prof_before(PROF_LZ_C, s);
     k_lz_c<V><<<ntiles, RSB_BLOCK, 0, s>>>(a, j, breakdown);
@@ -1704,14 +1982,11 @@ static int lanczos_run(const LevelGraph& G, const Tile* tiles, int ntiles, Unit*
     }
     return rc;
   }
-  // the staged step B (FP32) needs up to 2 * (M + 1) * (RSB_BLOCK + 4) floats of
+  // the staged step D2 (FP32) needs up to 2 * (M + 1) * (RSB_BLOCK + 4) floats of
   // dynamic shared memory (85 KB at M = 40)
-  if (sizeof(V) == 4) {
-    RSB_CK(cudaFuncSetAttribute(k_lz_bt<V>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)lz_bt_smem<V>(M + 1)));
-    RSB_CK(cudaFuncSetAttribute(k_lz_a2<V>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)lz_bt_smem<V>(M + 1)));
-  }
+  if constexpr (sizeof(V) == 4)
+    RSB_CK(cudaFuncSetAttribute(k_lz_d2<V>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)staged_smem<V>(M + 1)));
   cudaGraphExec_t exec = nullptr;
   std::vector<int> cap_pairs;
   if (use_graph) {
@@ -1738,7 +2013,7 @@ static int lanczos_run(const LevelGraph& G, const Tile* tiles, int ntiles, Unit*
   for (int cyc = 0; cyc < 100000; ++cyc) {
     if (exec) {
       cudaError_t e = cudaGraphLaunch(exec, s);
-      rsb_count_launch((sizeof(V) == 4 ? 4 : 3) * M + 5);  // the kernels of one cycle
+      rsb_count_launch(3 * M + 5);  // the kernels of one cycle
       if (e != cudaSuccess) {
         cudaGraphExecDestroy(exec);
         return rsb_set_cuda_error(e, "cudaGraphLaunch");
