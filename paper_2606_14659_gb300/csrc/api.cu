@@ -513,14 +513,20 @@ static int max_tile_rows(const std::vector<Tile>& tiles) {
 
 static void make_tiles(std::vector<Unit>& units, std::vector<Tile>& tiles, int rmin = RSB_MINR) {
   tiles.clear();
+  // rows per thread of a tile: at least rmin (memory-level parallelism), more
+  // on a level so large that it would exceed about RSB_TARGET_TILES tiles, and
+  // more for large units so that a unit has at most RSB_MAXTILES_PER_UNIT tiles
+  int64_t nlevel = 0;
+  for (const Unit& u : units) nlevel += u.nrows;
+  const int64_t rlevel = (nlevel + (int64_t)RSB_BLOCK * RSB_TARGET_TILES - 1) /
+                         ((int64_t)RSB_BLOCK * RSB_TARGET_TILES);
   for (size_t i = 0; i < units.size(); ++i) {
     Unit& u = units[i];
     const int64_t nr = u.nrows;
-    // rows per thread of a tile: at least RSB_MINR (memory-level parallelism),
-    // more for large units so that a unit has at most RSB_MAXTILES_PER_UNIT tiles
     int64_t R = (nr + (int64_t)RSB_BLOCK * RSB_MAXTILES_PER_UNIT - 1) /
                 ((int64_t)RSB_BLOCK * RSB_MAXTILES_PER_UNIT);
     if (R < rmin) R = rmin;
+    if (R < rlevel) R = rlevel;
     const int64_t tr = R * RSB_BLOCK;
     u.tile0 = (int32_t)tiles.size();
     int nt = 0;
