@@ -261,48 +261,6 @@ template <> struct Acc<float> {
   __device__ __forceinline__ double get() const { return (double)s - (double)c; }
 };
 
-// Packed pairs of FP32 values ({lo, hi} in one 64-bit register) and the
-// f32x2 arithmetic of sm_100 and later: one instruction operates on both
-// halves, each rounded as the scalar operation would be (.rn, no contraction).
-__device__ __forceinline__ unsigned long long f2_pack(float lo, float hi) {
-  unsigned long long r;
-  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
-  return r;
-}
-__device__ __forceinline__ void f2_unpack(unsigned long long r, float& lo, float& hi) {
-  asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(r));
-}
-__device__ __forceinline__ unsigned long long f2_add(unsigned long long a, unsigned long long b) {
-  unsigned long long r;
-  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
-  return r;
-}
-__device__ __forceinline__ unsigned long long f2_sub(unsigned long long a, unsigned long long b) {
-  unsigned long long r;
-  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
-  return r;
-}
-__device__ __forceinline__ unsigned long long f2_mul(unsigned long long a, unsigned long long b) {
-  unsigned long long r;
-  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
-  return r;
-}
-
-// Two compensated FP32 sums advanced together by packed instructions: the
-// same roundings, step for step, as two Acc<float>.
-struct Acc2 {
-  unsigned long long s = 0ull, c = 0ull;  // all-zero bits: +0.0f in both halves
-  __device__ __forceinline__ void add(unsigned long long x) {
-    const unsigned long long y = f2_sub(x, c);
-    const unsigned long long t = f2_add(s, y);
-    c = f2_sub(f2_sub(t, s), y);
-    s = t;
-  }
-  __device__ __forceinline__ void split(Acc<float>& lo, Acc<float>& hi) const {
-    f2_unpack(s, lo.s, hi.s);
-    f2_unpack(c, lo.c, hi.c);
-  }
-};
 
 // Warp total of per-lane accumulators, valid in lane 0.  FP64: plain
 // butterfly.  FP32: the lanes' Kahan states (value s - c) are merged in FP32
