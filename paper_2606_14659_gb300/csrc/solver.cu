@@ -605,7 +605,7 @@ __device__ void d2_finish(double* av, double* gz, int nb, int nd, int j, double 
 // [g_b (b < nb), v.z], nb = 1 + nd + j.
 // ----------------------------------------------------------------------------
 template <typename V>
-__global__ void __launch_bounds__(RSB_BLOCK, 2) k_lz_d2(LzArgs<V> a, int j, GridBar* gb) {
+__global__ void __launch_bounds__(RSB_BLOCK, 3) k_lz_d2(LzArgs<V> a, int j, GridBar* gb) {
   extern __shared__ __align__(128) unsigned char d2_sh[];
   constexpr int AL = BulkRows<V>::AL, CRB = BulkRows<V>::CRB;
   __shared__ __align__(8) uint64_t bar[ST_NB];
@@ -1984,9 +1984,14 @@ static int lanczos_run(const LevelGraph& G, const Tile* tiles, int ntiles, Unit*
   }
   // the staged step D2 (FP32) needs up to 2 * (M + 1) * (RSB_BLOCK + 4) floats of
   // dynamic shared memory (85 KB at M = 40)
-  if constexpr (sizeof(V) == 4)
+  if constexpr (sizeof(V) == 4) {
     RSB_CK(cudaFuncSetAttribute(k_lz_d2<V>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)staged_smem<V>(M + 1)));
+    // the whole carveout as shared memory: D2 is bound by the CTAs per SM that
+    // its staged chunks leave room for (two at the default carveout)
+    RSB_CK(cudaFuncSetAttribute(k_lz_d2<V>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                cudaSharedmemCarveoutMaxShared));
+  }
   cudaGraphExec_t exec = nullptr;
   std::vector<int> cap_pairs;
   if (use_graph) {
