@@ -605,7 +605,7 @@ __device__ void d2_finish(double* av, double* gz, int nb, int nd, int j, double 
 // [g_b (b < nb), v.z], nb = 1 + nd + j.
 // ----------------------------------------------------------------------------
 template <typename V>
-__global__ void __launch_bounds__(RSB_BLOCK, 3) k_lz_d2(LzArgs<V> a, int j, GridBar* gb) {
+__global__ void __launch_bounds__(RSB_BLOCK, 4) k_lz_d2(LzArgs<V> a, int j, GridBar* gb) {
   extern __shared__ __align__(128) unsigned char d2_sh[];
   constexpr int AL = BulkRows<V>::AL, CRB = BulkRows<V>::CRB;
   __shared__ __align__(8) uint64_t bar[ST_NB];

@@ -1,4 +1,4 @@
-"""rsb_laplacian_apply_noalloc against rsb_laplacian_apply.
+"""rsb_laplacian_apply_noalloc against rsb_laplacian_apply and the oracle.
 
 The no-allocation entry point serves callers that cannot call cudaMalloc (a
 framework's caching allocator holds the device, a region where the implicit
@@ -20,6 +20,7 @@ pytestmark = pytest.mark.gpu
 if not torch.cuda.is_available():  # pragma: no cover
     pytest.skip("no GPU", allow_module_level=True)
 
+import oracle as O  # noqa: E402
 import paper_2606_14659_gb300 as R  # noqa: E402
 
 
@@ -40,6 +41,7 @@ def test_noalloc_matches_allocating_entry_two_calls():
         xi = rng.integers(-9, 9, g.n).astype(np.float64)
         y, ref = _apply_both(g, xi)
         assert np.array_equal(y, ref)                  # integer vectors: exact
+        assert np.array_equal(y, O.laplacian_apply(g, xi))
         xr = rng.standard_normal(g.n)
         y, ref = _apply_both(g, xr)
         scale = np.abs(xr).max() * 56.0
