@@ -511,22 +511,28 @@ static int max_tile_rows(const std::vector<Tile>& tiles) {
   return m;
 }
 
-static void make_tiles(std::vector<Unit>& units, std::vector<Tile>& tiles, int rmin = RSB_MINR) {
+// mesh_rows[i]: the element count of the mesh unit i belongs to (empty: the
+// units are parts of one mesh, whose rows they cover)
+static void make_tiles(std::vector<Unit>& units, std::vector<Tile>& tiles, int rmin = RSB_MINR,
+                       const std::vector<int64_t>& mesh_rows = {}) {
   tiles.clear();
   // rows per thread of a tile: at least rmin (memory-level parallelism), more
-  // on a level so large that it would exceed about RSB_TARGET_TILES tiles, and
-  // more for large units so that a unit has at most RSB_MAXTILES_PER_UNIT tiles
-  int64_t nlevel = 0;
-  for (const Unit& u : units) nlevel += u.nrows;
-  const int64_t rlevel = (nlevel + (int64_t)RSB_BLOCK * RSB_TARGET_TILES - 1) /
-                         ((int64_t)RSB_BLOCK * RSB_TARGET_TILES);
+  // in a mesh so large that one of its levels would exceed about
+  // RSB_TARGET_TILES tiles, and more for large units so that a unit has at
+  // most RSB_MAXTILES_PER_UNIT tiles.  The rule looks at the unit's own mesh,
+  // so a mesh is tiled alike alone and in a batch (same sums, same bits).
+  int64_t nall = 0;
+  for (const Unit& u : units) nall += u.nrows;
   for (size_t i = 0; i < units.size(); ++i) {
     Unit& u = units[i];
     const int64_t nr = u.nrows;
+    const int64_t nmesh = mesh_rows.empty() ? nall : mesh_rows[i];
+    const int64_t rmesh = (nmesh + (int64_t)RSB_BLOCK * RSB_TARGET_TILES - 1) /
+                          ((int64_t)RSB_BLOCK * RSB_TARGET_TILES);
     int64_t R = (nr + (int64_t)RSB_BLOCK * RSB_MAXTILES_PER_UNIT - 1) /
                 ((int64_t)RSB_BLOCK * RSB_MAXTILES_PER_UNIT);
     if (R < rmin) R = rmin;
-    if (R < rlevel) R = rlevel;
+    if (R < rmesh) R = rmesh;
     const int64_t tr = R * RSB_BLOCK;
     u.tile0 = (int32_t)tiles.size();
     int nt = 0;
@@ -941,7 +947,9 @@ static int run_rsb(Ctx& c, const std::vector<MeshIn>& meshes, const std::vector<
       }
       if (!su.empty()) {
         std::vector<Tile> st2;
-        make_tiles(su, st2);
+        std::vector<int64_t> su_mesh;
+        for (const Unit& u : su) su_mesh.push_back(meshes[segs[u.seg].mesh].n);
+        make_tiles(su, st2, RSB_MINR, su_mesh);
         if ((rc = devbuf_reserve(c.sunits, sizeof(Unit) * su.size()))) return rc;
         if ((rc = devbuf_reserve(c.stiles, sizeof(Tile) * st2.size()))) return rc;
         if ((rc = devbuf_reserve(c.hist, sizeof(int) * 256 * su.size()))) return rc;
@@ -992,7 +1000,9 @@ static int run_rsb(Ctx& c, const std::vector<MeshIn>& meshes, const std::vector<
       hunits.push_back(u);
     }
     std::vector<Tile> htiles;
-    make_tiles(hunits, htiles, o.tile_rows > 0 ? o.tile_rows : RSB_MINR);
+    std::vector<int64_t> hmesh;
+    for (const Unit& u : hunits) hmesh.push_back(meshes[segs[u.seg].mesh].n);
+    make_tiles(hunits, htiles, o.tile_rows > 0 ? o.tile_rows : RSB_MINR, hmesh);
     trace_mark(c.s, "level %d components and units", level);
     if ((rc = split_units(c, G, hunits, htiles, o, rs))) return rc;
     trace_mark(c.s, "level %d split (%d units)", level, (int)hunits.size());

@@ -158,6 +158,19 @@ def test_c4_batch_equals_separate_calls(c4):
         assert np.array_equal(p.cpu().numpy(), alone.cpu().numpy())
 
 
+def test_batch_with_a_large_mesh_equals_separate_calls():
+    # a mesh above 256 x 2432 rows gets longer tiles than the library's minimum; the rule
+    # looks at each unit's own mesh, so both meshes are tiled (and summed) as when alone
+    big = box_graph_deleted(120, 110, 100, 0.05, 3, "vertex")
+    small = box_graph(30, 20, 10)
+    assert big.n > 2 * 256 * 2432 and small.n < 256 * 2432  # 3 rows per thread against 2
+    opts = R.options(precision="mixed")
+    parts, _, _ = R.rsb_partition_batch([R.graph(big), R.graph(small)], [4, 4], opts)
+    for g, p in zip((big, small), parts):
+        alone, _, _ = R.rsb_partition(R.graph(g), 4, opts, allow_noconv=True)
+        assert np.array_equal(p.cpu().numpy(), alone.cpu().numpy())
+
+
 def test_c5_partition_mixed_lanczos():
     """The options bench.py times on this workload."""
     g = box_graph_deleted(256, 256, 256, 0.05, 20261, "vertex")
